@@ -1,0 +1,422 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+Each test compares the oracle with something that is not the oracle: exact
+solutions of the NLSE, closed-form discrete spectra, brute force over the
+paper's printed stencil tables, polynomial exactness, numbers printed in the
+paper, invariants.  Chosen so that a dropped term, a wrong sign or index or a
+transposed operand in the oracle fails at least one of them.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1203_1263_gb300 import workloads as W
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def rel_l2(x, ref):
+    return float(np.linalg.norm(np.ravel(x - ref)) / np.linalg.norm(np.ravel(ref)))
+
+
+def rk4_amplification(z):
+    """Classic RK4 applied to y' = lambda y multiplies y by 1 + z + z^2/2 + z^3/6 + z^4/24, z = lambda dt."""
+    return 1 + z + z * z / 2 + z ** 3 / 6 + z ** 4 / 24
+
+
+def cd_symbol(theta, h):
+    """Eigenvalue of the 3-point second difference on exp(i theta j) or sin(theta j)."""
+    return -(4.0 / (h * h)) * math.sin(theta / 2) ** 2
+
+
+# ---------------------------------------------------------------------------
+# P1, P2: exact solitons and spatial convergence orders
+# ---------------------------------------------------------------------------
+
+def _orders(errs):
+    return [math.log2(errs[i] / errs[i + 1]) for i in range(len(errs) - 1)]
+
+
+@pytest.mark.parametrize("order,expect,tol", [(2, 2.0, 0.15), (4, 4.0, 0.3)])
+def test_bright_soliton_convergence(order, expect, tol):
+    """Moving bright soliton (exact solution), Dirichlet walls far away."""
+    errs = []
+    for n in (501, 1001, 2001):
+        p = W.bright_soliton_1d(order=order, n=n, t_end=2.0)
+        out, _ = O.run_problem(p)
+        exact = W.bright_soliton(p.extra["x"], p.extra["t_end"])
+        errs.append(rel_l2(out, exact))
+    for o in _orders(errs):
+        assert abs(o - expect) < tol, (errs, _orders(errs))
+    assert errs[-1] < (2e-3 if order == 2 else 3e-6)
+
+
+@pytest.mark.parametrize("order,expect,tol", [(2, 2.0, 0.15), (4, 4.0, 0.3)])
+def test_dark_soliton_msd_convergence(order, expect, tol):
+    """The paper's co-moving dark soliton (Sec. 4, Eq. soliton) with the MSD wall."""
+    errs = []
+    for h in (0.2, 0.1, 0.05):
+        p = W.dark_soliton_1d(order=order, h=h, L=30.0, t_end=2.0)
+        out, _ = O.run_problem(p)
+        exact = W.dark_soliton(p.extra["x"], p.extra["t_end"])
+        errs.append(rel_l2(out, exact))
+    for o in _orders(errs):
+        assert abs(o - expect) < tol, (errs, _orders(errs))
+
+
+def stationary_dark(x, a, s, kappa):
+    """A tanh(kappa x) with A^2 = -2 a kappa^2 / s solves a psi'' - V0 psi + s|psi|^2 psi = 0
+    for the constant potential V0 = -2 a kappa^2 (s < 0): a time-independent exact
+    solution, so fixed (Dirichlet) walls are exact wherever they are placed."""
+    return math.sqrt(-2.0 * a * kappa * kappa / s) * np.tanh(kappa * x)
+
+
+@pytest.mark.parametrize("order,expect,tol", [(2, 2.0, 0.2), (4, 4.0, 0.35)])
+@pytest.mark.parametrize("dims,axis", [(1, 0), (2, 0), (2, 1), (3, 2)])
+def test_stationary_dark_soliton_dirichlet(order, expect, tol, dims, axis):
+    """Walls at kappa x = -1.2 and 1.8, inside the core, so the Dirichlet
+    Laplacian form (Eq. BCDlap) carries a non-zero Laplacian into 2SHOC."""
+    a, s, kappa, T = 0.8, -1.0, 1.0, 0.5
+    errs = []
+    for h in (0.1, 0.05, 0.025):
+        n = int(round(3.0 / h)) + 1
+        x = -1.2 + h * np.arange(n)
+        prof = stationary_dark(x, a, s, kappa)
+        shape = [5] * dims
+        shape[axis] = n
+        sh = [1] * dims
+        sh[axis] = n
+        psi0 = np.ascontiguousarray(np.broadcast_to(prof.reshape(sh), shape)).astype(np.complex128)
+        V = np.full(shape, -2.0 * a * kappa * kappa)
+        dt = h * h / 8.0
+        out = O.rk4(psi0, h, a, s, dt, int(round(T / dt)), V, W.BC_DIRICHLET, order)
+        errs.append(rel_l2(out, psi0))
+    # With 5-point transverse Dirichlet walls the interior is pinned hard, so
+    # more than the scheme's order may show; never less.
+    for o in _orders(errs):
+        assert o > expect - tol, (errs, _orders(errs))
+    assert errs[-1] < (1e-4 if order == 2 else 1e-7)
+
+
+# ---------------------------------------------------------------------------
+# P3: linear sine modes are exact discrete eigenfunctions
+# ---------------------------------------------------------------------------
+
+SINE_CASES = [((41,), (3,)), ((21, 17), (2, 5)), ((11, 13, 9), (2, 3, 1))]
+
+
+@pytest.mark.parametrize("shape,modes", SINE_CASES)
+@pytest.mark.parametrize("order", [2, 4])
+def test_sine_modes_exact_rk4(shape, modes, order):
+    """s = 0, V = 0, Dirichlet zero walls: Psi^n = R(i a dt lambda)^n Psi^0 where
+    lambda = sum sigma (CD) or sum (sigma - h^2 sigma^2 / 12) (2SHOC)."""
+    h, a, dt, n = 0.3, 0.7, 0.004, 25
+    sig = [cd_symbol(math.pi * m / (N - 1), h) for N, m in zip(shape, modes)]
+    lam = sum(sig) if order == 2 else sum(s_ - h * h * s_ * s_ / 12 for s_ in sig)
+    psi0 = W.sine_mode(shape, modes)
+    out = O.rk4(psi0, h, a, 0.0, dt, n, None, W.BC_DIRICHLET, order)
+    expect = rk4_amplification(1j * a * dt * lam) ** n * psi0
+    assert rel_l2(out, expect) < 1e-13
+
+
+@pytest.mark.parametrize("shape,modes", SINE_CASES)
+@pytest.mark.parametrize("order", [2, 4])
+def test_sine_mode_laplacian_eigenvalue(shape, modes, order):
+    h = 0.25
+    sig = [cd_symbol(math.pi * m / (N - 1), h) for N, m in zip(shape, modes)]
+    lam = sum(sig) if order == 2 else sum(s_ - h * h * s_ * s_ / 12 for s_ in sig)
+    psi0 = W.sine_mode(shape, modes)
+    D, L = O.laplacian(psi0, h, 1.0, 0.0, None, W.BC_DIRICHLET, order)
+    inner = tuple(slice(1, -1) for _ in shape)
+    assert np.max(np.abs(L[inner] - lam * psi0[inner])) < 1e-11 * abs(lam)
+
+
+def test_temporal_order_four():
+    """Global RK4 error against the semi-discrete solution exp(i a lambda t) falls as dt^4."""
+    shape, modes, h, a, T = (33,), (5,), 0.2, 1.0, 0.5
+    lam = cd_symbol(math.pi * modes[0] / (shape[0] - 1), h)
+    psi0 = W.sine_mode(shape, modes)
+    errs = []
+    for nsteps in (40, 80, 160):
+        dt = T / nsteps
+        out = O.rk4(psi0, h, a, 0.0, dt, nsteps, None, W.BC_DIRICHLET, 2)
+        errs.append(rel_l2(out, np.exp(1j * a * lam * T) * psi0))
+    for o in _orders(errs):
+        assert abs(o - 4.0) < 0.1, errs
+
+
+# ---------------------------------------------------------------------------
+# P4: stability bound (printed values) and its sharpness
+# ---------------------------------------------------------------------------
+
+def _golden_bounds():
+    rows = []
+    for line in open(os.path.join(GOLDEN, "stability_bounds.txt")):
+        line = line.split("#")[0].split()
+        if line:
+            rows.append((int(line[0]), int(line[1]), float(line[2]), float(line[3]), float(line[4]),
+                         float(line[5])))
+    return rows
+
+
+@pytest.mark.parametrize("row", _golden_bounds())
+def test_stability_bound_printed(row):
+    d, order, h, a, printed, tol = row
+    got = O.stability_bound(d, h, a, order)
+    assert abs(got - printed) <= tol * printed, (got, printed)
+
+
+@pytest.mark.parametrize("order", [2, 4])
+def test_stability_bound_is_sharp(order):
+    """The highest sine mode grows just above the bound and does not just below it."""
+    N, h, a = 101, 0.1, 1.0
+    psi0 = W.sine_mode((N,), (N - 2,))
+    bound = O.stability_bound(1, h, a, order)
+    above = O.rk4(psi0, h, a, 0.0, 1.02 * bound, 200, None, W.BC_DIRICHLET, order)
+    below = O.rk4(psi0, h, a, 0.0, 0.98 * bound, 200, None, W.BC_DIRICHLET, order)
+    n0 = np.linalg.norm(psi0)
+    assert np.linalg.norm(above) > 10 * n0
+    assert np.linalg.norm(below) <= n0 * (1 + 1e-12)
+
+
+# ---------------------------------------------------------------------------
+# P5: uniform backgrounds and plane waves under MSD follow the scalar RK4 iterate
+# ---------------------------------------------------------------------------
+
+def scalar_rk4(z, dt, nsteps, rate):
+    """Classic RK4 on z' = i rate(|z|^2) z."""
+    f = lambda y: 1j * rate(abs(y) ** 2) * y
+    for _ in range(nsteps):
+        k1 = f(z); k2 = f(z + dt / 2 * k1); k3 = f(z + dt / 2 * k2); k4 = f(z + dt * k3)
+        z = z + dt / 6 * (k1 + 2 * k2 + 2 * k3 + k4)
+    return z
+
+
+@pytest.mark.parametrize("shape", [(9,), (7, 8), (5, 6, 7)])
+@pytest.mark.parametrize("order", [2, 4])
+def test_uniform_background_msd(shape, order):
+    rho, phi, s, a, dt, n = 1.3, 0.4, -1.0, 0.5, 0.01, 30
+    z0 = math.sqrt(rho) * complex(math.cos(phi), math.sin(phi))
+    psi0 = np.full(shape, z0, dtype=np.complex128)
+    out = O.rk4(psi0, 0.2, a, s, dt, n, None, W.BC_MSD, order)
+    z = scalar_rk4(z0, dt, n, lambda m2: s * m2)
+    assert np.max(np.abs(out - z)) < 1e-13
+
+
+@pytest.mark.parametrize("shape,k", [((12,), (0.9,)), ((10, 11), (0.7, -0.4)), ((8, 9, 10), (0.6, -0.5, 0.3))])
+@pytest.mark.parametrize("order", [2, 4])
+def test_plane_wave_msd(shape, k, order):
+    """sqrt(rho) exp(i k.x) is an exact discrete solution under MSD: every site is
+    z_n exp(i k.x) with z' = i(a lambda_k + s|z|^2) z.  Pins the MSD time-derivative
+    form at faces, edges and corners and, for 2SHOC, the MSD Laplacian form."""
+    h, rho, s, a, dt, n = 0.3, 0.8, 1.0, 0.6, 0.003, 40
+    sig = [cd_symbol(kk * h, h) for kk in k]
+    lam = sum(sig) if order == 2 else sum(s_ - h * h * s_ * s_ / 12 for s_ in sig)
+    grids = np.meshgrid(*[np.arange(N) * h for N in shape], indexing="ij")
+    phase = np.exp(1j * sum(kk * g for kk, g in zip(k, grids)))
+    psi0 = math.sqrt(rho) * phase
+    out = O.rk4(psi0, h, a, s, dt, n, None, W.BC_MSD, order)
+    z = scalar_rk4(complex(math.sqrt(rho)), dt, n, lambda m2: a * lam + s * m2)
+    assert np.max(np.abs(out - z * phase)) < 1e-12
+
+
+# ---------------------------------------------------------------------------
+# P6: brute force over the printed stencil tables; polynomial exactness
+# ---------------------------------------------------------------------------
+
+def _frac(x):
+    if "/" in x:
+        a, b = x.split("/")
+        return float(a) / float(b)
+    return float(x)
+
+
+def _tables():
+    t = {}
+    for line in open(os.path.join(GOLDEN, "stencils_2shoc.txt")):
+        f = line.split("#")[0].split()
+        if not f:
+            continue
+        d, step, operand, scale = int(f[0]), int(f[1]), f[2], f[3]
+        off = tuple(int(v) for v in f[4:4 + d])
+        w = _frac(f[4 + d])
+        t.setdefault((d, step), []).append((operand, scale, off, w))
+    return t
+
+
+def _apply(entries, fields, h, site):
+    scales = {"inv_h2": 1 / h ** 2, "m1_12": -1 / 12, "one": 1.0, "inv_6h2": 1 / (6 * h * h)}
+    acc = 0.0
+    for operand, scale, off, w in entries:
+        idx = tuple(s_ + o for s_, o in zip(site, off))
+        acc += scales[scale] * w * fields[operand][idx]
+    return acc
+
+
+@pytest.mark.parametrize("shape", [(11,), (8, 9), (6, 7, 8)])
+def test_stencil_tables_brute_force(shape):
+    """D and the 2SHOC Laplacian equal a naive sum over the paper's tables at
+    every site two or more cells from the walls."""
+    tab = _tables()
+    d = len(shape)
+    h = 0.37
+    psi = W.random_field(shape, seed=11)
+    D_or, L_or = O.laplacian(psi, h, 1.0, 0.0, None, W.BC_DIRICHLET, 4)
+    D_bf = np.zeros_like(psi)
+    for site in np.ndindex(*shape):
+        if all(0 < i < n - 1 for i, n in zip(site, shape)):
+            D_bf[site] = _apply(tab[(d, 1)], {"psi": psi}, h, site)
+    scale = np.max(np.abs(D_bf))
+    for site in np.ndindex(*shape):
+        if all(1 < i < n - 2 for i, n in zip(site, shape)):
+            assert abs(D_or[site] - D_bf[site]) < 1e-13 * scale
+            ref = _apply(tab[(d, 2)], {"psi": psi, "D": D_bf}, h, site)
+            assert abs(L_or[site] - ref) < 1e-13 * scale, site
+
+
+def _poly_field(shape, h, degree, seed):
+    """Random polynomial of total degree <= degree and its exact Laplacian."""
+    d = len(shape)
+    u = W.uniform(seed, 64)
+    coords = np.meshgrid(*[np.arange(n) * h - 0.4 for n in shape], indexing="ij")
+    terms = [e for e in np.ndindex(*([degree + 1] * d)) if sum(e) <= degree]
+    f = np.zeros(shape)
+    lap = np.zeros(shape)
+    for t_i, e in enumerate(terms):
+        c = u[t_i % 64] - 0.5
+        mono = np.ones(shape)
+        for ax in range(d):
+            mono = mono * coords[ax] ** e[ax]
+        f += c * mono
+        for ax in range(d):
+            if e[ax] >= 2:
+                m = np.ones(shape) * e[ax] * (e[ax] - 1)
+                for bx in range(d):
+                    m = m * coords[bx] ** (e[bx] - (2 if bx == ax else 0))
+                lap += c * m
+    return f, lap
+
+
+@pytest.mark.parametrize("shape", [(13,), (9, 10), (7, 8, 7)])
+@pytest.mark.parametrize("order,degree", [(2, 3), (4, 5)])
+def test_polynomial_exactness(shape, order, degree):
+    h = 0.11
+    f, lap = _poly_field(shape, h, degree, seed=5)
+    psi = (f + 0.5j * f).astype(np.complex128)
+    _, L = O.laplacian(psi, h, 1.0, 0.0, None, W.BC_DIRICHLET, order)
+    m = 2 if order == 4 else 1
+    inner = tuple(slice(m, n - m) for n in shape)
+    tol = 1e-9 * max(1.0, np.max(np.abs(f)) / h ** 2)
+    assert np.max(np.abs(L[inner] - (lap + 0.5j * lap)[inner])) < tol
+    # one degree higher is no longer exact (the test has teeth)
+    f2, lap2 = _poly_field(shape, h, degree + 1, seed=6)
+    _, L2 = O.laplacian(f2.astype(np.complex128), h, 1.0, 0.0, None, W.BC_DIRICHLET, order)
+    assert np.max(np.abs(L2[inner].real - lap2[inner])) > 1e3 * tol
+
+
+# ---------------------------------------------------------------------------
+# P7, P8: mass and energy
+# ---------------------------------------------------------------------------
+
+def test_mass_closed_form_and_exact_sum():
+    shape, h = (6, 7, 8), 0.3
+    psi = np.full(shape, 0.5 + 0.25j)
+    assert abs(O.mass(psi, h) - (0.3125 * h ** 3 * 336)) < 1e-15
+    psi = W.random_field((40, 50), seed=3)
+    exact = math.fsum((np.abs(psi) ** 2).ravel().tolist()) * h ** 2
+    assert abs(O.mass(psi, h) - exact) <= 2e-16 * exact
+
+
+@pytest.mark.parametrize("shape,modes", SINE_CASES)
+@pytest.mark.parametrize("order", [2, 4])
+def test_energy_closed_form(shape, modes, order):
+    """For a sine mode with zero walls Lap Psi = lambda Psi, so
+    E = h^d sum_interior [(-a lambda + V)|Psi|^2 - (s/2)|Psi|^4]."""
+    h, a, s = 0.3, 0.7, -0.9
+    sig = [cd_symbol(math.pi * m / (N - 1), h) for N, m in zip(shape, modes)]
+    lam = sum(sig) if order == 2 else sum(s_ - h * h * s_ * s_ / 12 for s_ in sig)
+    psi = 0.8 * W.sine_mode(shape, modes)
+    V = W.random_potential(shape, seed=9, scale=2.0)
+    inner = tuple(slice(1, -1) for _ in shape)
+    m2 = np.abs(psi[inner]) ** 2
+    terms = (-a * lam + V[inner]) * m2 - 0.5 * s * m2 * m2
+    expect = h ** len(shape) * math.fsum(terms.ravel().tolist())
+    got = O.energy(psi, h, a, s, V, W.BC_DIRICHLET, order)
+    assert abs(got - expect) < 1e-12 * abs(expect)
+
+
+@pytest.mark.parametrize("bc", [W.BC_DIRICHLET, W.BC_MSD])
+def test_energy_counts_interior_sites_only(bc):
+    """Every term of the energy density carries a factor of the site's own Psi,
+    so a field that vanishes on the interior has zero energy whatever its walls hold."""
+    shape = (6, 7, 5)
+    psi = W.random_field(shape, seed=41)
+    psi[1:-1, 1:-1, 1:-1] = 0
+    V = W.random_potential(shape, seed=42, scale=2.0)
+    assert O.energy(psi, 0.3, 0.7, 1.3, V, bc, 4) == 0.0
+    assert O.energy(psi, 0.3, 0.7, 1.3, V, bc, 2) == 0.0
+
+
+@pytest.mark.parametrize("order", [2, 4])
+def test_mass_nonincreasing_linear_dirichlet(order):
+    """s = 0, zero walls: RK4 has |R(iy)| <= 1 inside the bound, so the mass never grows."""
+    shape, h, a = (12, 13), 0.2, 1.0
+    psi = W.random_field(shape, seed=21)
+    psi[0, :] = psi[-1, :] = psi[:, 0] = psi[:, -1] = 0
+    V = W.random_potential(shape, seed=22, scale=3.0)
+    dt = 0.8 * O.stability_bound(2, h, a, order, vmax=3.0)
+    m_prev = O.mass(psi, h)
+    for _ in range(20):
+        psi = O.rk4(psi, h, a, 0.0, dt, 1, V, W.BC_DIRICHLET, order)
+        m = O.mass(psi, h)
+        assert m <= m_prev * (1 + 1e-14)
+        m_prev = m
+
+
+@pytest.mark.parametrize("order", [2, 4])
+def test_bright_soliton_mass_energy_drift(order):
+    """Bright soliton to t = 2 at h = 0.05, dt = h^2/8: |dM|/M <= 1e-9, |dE|/|E| <= 1e-8."""
+    p = W.bright_soliton_1d(order=order, n=2001, t_end=2.0)
+    out, _ = O.run_problem(p)
+    M0, M1 = O.mass(p.psi0, p.h), O.mass(out, p.h)
+    E0 = O.energy(p.psi0, p.h, p.a, p.s, None, p.bc, p.order)
+    E1 = O.energy(out, p.h, p.a, p.s, None, p.bc, p.order)
+    assert abs(M1 - M0) <= 1e-9 * M0
+    assert abs(E1 - E0) <= 1e-8 * abs(E0)
+
+
+# ---------------------------------------------------------------------------
+# P9, P10: symmetry and split continuation
+# ---------------------------------------------------------------------------
+
+def test_vortex_rotation_symmetry():
+    """Charge-1 vortex line in the axisymmetric trap on a square xy grid:
+    Psi(-y, x, z) = i Psi(x, y, z) for all time."""
+    p = W.trap_vortex_3d(shape=(11, 15, 15), h=0.6, noise=0.0)
+    dt = 0.8 * O.stability_bound(3, p.h, p.a, 4, p.vmax(), abs(p.s) * np.max(np.abs(p.psi0)) ** 2)
+    out = O.rk4(p.psi0, p.h, p.a, p.s, dt, 12, p.V, p.bc, p.order)
+    n = 15
+    jy, ix = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    lhs = out[:, ix, n - 1 - jy]
+    rhs = 1j * out[:, jy, ix]
+    assert np.max(np.abs(lhs - rhs)) < 1e-13
+    assert np.max(np.abs(out - p.psi0)) > 1e-3      # it did evolve
+
+
+@pytest.mark.parametrize("bc", [W.BC_DIRICHLET, W.BC_MSD])
+def test_split_continuation_bitwise(bc):
+    psi = W.random_field((9, 10), seed=31)
+    V = W.random_potential((9, 10), seed=32)
+    a1 = O.rk4(psi, 0.3, 0.8, 1.0, 0.002, 7, V, bc, 4)
+    a2 = O.rk4(O.rk4(psi, 0.3, 0.8, 1.0, 0.002, 3, V, bc, 4), 0.3, 0.8, 1.0, 0.002, 4, V, bc, 4)
+    assert np.array_equal(a1, a2)
+
+
+def test_bad_arguments_rejected():
+    with pytest.raises(ValueError):
+        O.rk4(np.zeros((2, 5), np.complex128), 0.1, 1.0, 1.0, 0.001, 1)
+    with pytest.raises(ValueError):
+        O.rk4(np.zeros((5, 5), np.complex128), 0.1, 1.0, 1.0, 0.001, 1, order=3)
