@@ -1,0 +1,343 @@
+#!/usr/bin/env python
+"""RK4 NLSE benchmark: site-updates per second of the 3D Gross-Pitaevskii
+trap-vortex problem (2SHOC Laplacian, MSD walls) on one GB300.
+
+One bench step is one RK4 time step over the whole grid (four fused stage
+kernels).  `value` is timed on the device with CUDA events around K steps
+whose inputs are already resident in HBM; every array is larger than L2.
+`e2e` is the same metric through the public API with Psi copied from and
+back to pinned host memory around each chunk of steps (the paper's frames).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank integrates its own replica of the problem
+on its own GPU (the method has no data exchange between problems); rank 0
+prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import platform
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_1203_1263_gb300 import workloads as W  # noqa: E402
+
+WORKLOADS = {
+    "trap_vortex_3d_256x256x512": dict(shape=(512, 256, 256)),
+    "trap_vortex_3d_87x87x203": dict(shape=(203, 87, 87)),
+}
+METRIC = "RK4 site-updates/s (Gsite*step/s)"
+UNIT = "Gsite*step/s"
+# algorithmic HBM bytes per site per RK4 step of the stage-streaming form
+# (stage 1 reads Psi, V and writes K_tot, Psi_tmp; stages 2/3 read Psi_stage,
+# V, Psi^n, K_tot and write K_tot, Psi_next; stage 4 reads Psi_tmp, V, K_tot,
+# Psi^n and writes Psi^{n+1}):
+ALG_BYTES = {  # dtype -> (with V, without V)
+    "c128": (304, 272),
+    "c64": (152, 136),
+    "c64_acc64": (176, 160),
+}
+CHUNK = 56   # steps per frame in the end-to-end measurement (the 87x87x203 run's chunk size)
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_gpu{gpu_index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.gpu)], stdout=self.fh,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) >= 9:
+                rows.append(f)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def build_problem(name):
+    spec = WORKLOADS[name]
+    return W.trap_vortex_3d(shape=spec["shape"])
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    from paper_1203_1263_gb300.integrator import Integrator, max_dt
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    p = build_problem(args.workload)
+    s_rho = abs(p.s) * float(np.max(np.abs(p.psi0))) ** 2
+    dt = 0.8 * max_dt(3, p.h, p.a, p.order, p.vmax(), s_rho)
+    sites = p.sites
+    stream = torch.cuda.Stream(dev)
+
+    def timed(dtype, K, Wm):
+        with torch.cuda.stream(stream):
+            g = Integrator(p.psi0, p.h, p.a, p.s, p.V, "msd", p.order, dtype, device=dev, stream=stream)
+            g.step(Wm, dt)
+            g.sync()
+            barrier()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            clk = ClockSampler(local_rank)
+            clk.start()
+            w0 = time.perf_counter()
+            e0.record(stream)
+            g.step(K, dt)
+            e1.record(stream)
+            e1.synchronize()
+            wall = time.perf_counter() - w0
+            clocks = clk.stop()
+            ms = e0.elapsed_time(e1)
+            g.sync()
+            barrier()
+        return g, ms, wall, clocks
+
+    K, Wm = args.steps, args.warmup
+    g64, ms, wall, clocks = timed(args.dtype, K, Wm)
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    value = world * sites * K / (ms_max * 1e-3) / 1e9
+
+    result = None
+    if rank == 0:
+        hbm_peak, peak_kind = peaks()
+        bytes_site = ALG_BYTES[args.dtype][0 if p.V is not None else 1]
+        step_s = ms_max * 1e-3 / K
+        achieved = sites * bytes_site / step_s / 1e9
+        roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_peak, "unit": "GB/s",
+                "frac": round(achieved / hbm_peak, 4), "traffic": None, "peak_kind": peak_kind,
+                "kernel": "k_stage (4 fused RK4 stages per step)",
+                "alg_bytes_per_site_step": bytes_site}
+        result = {
+            "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world, "steps": K, "warmup": Wm,
+            "ms_per_step": round(ms_max / K, 4), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": {"c128": "f64", "c64": "f32", "c64_acc64": "f32+f64acc"}[args.dtype],
+            "data": "synthetic (seeded trap-vortex IC, no dataset)",
+            "config": {"workload": args.workload, "grid": list(p.shape), "h": p.h, "a": p.a, "s": p.s,
+                       "order": p.order, "bc": "msd", "dt": dt, "precision": args.dtype,
+                       "l2": "inputs larger than L2 (%.0f MB per state array)" % (sites * 16 / 1e6),
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "roofline": roof, "clocks": clocks, "gpu_launches": 4 * K,
+        }
+
+    # ---- other precision forms on the same problem (speed-up over FP64 at a stated accuracy) ----
+    if not args.no_forms and rank == 0:
+        ref_state = g64.numpy()
+        forms = {}
+        for dt_name in ("c64", "c64_acc64"):
+            if dt_name == args.dtype:
+                continue
+            g2, ms2, _, _ = timed(dt_name, K, Wm)
+            st = g2.numpy().astype(np.complex128)
+            rl2 = float(np.linalg.norm((st - ref_state).ravel()) / np.linalg.norm(ref_state.ravel()))
+            v2 = sites * K / (ms2 * 1e-3) / 1e9
+            b2 = ALG_BYTES[dt_name][0 if p.V is not None else 1]
+            ach = sites * b2 / (ms2 * 1e-3 / K) / 1e9
+            forms[dt_name] = {"value": round(v2, 4), "unit": UNIT, "speedup_vs_f64": round(v2 / value, 3),
+                              "rel_l2_vs_f64_gpu": rl2, "hbm_gbs": round(ach, 1),
+                              "hbm_frac": round(ach / peaks()[0], 4)}
+            g2.close()
+        result["forms"] = forms
+
+    # ---- end to end through the public API: pinned host Psi in, CHUNK steps, Psi and mass out ----
+    if not args.no_e2e:
+        import torch
+        host_np = p.psi0.astype(np.complex64) if args.dtype == "c64" else p.psi0
+        host_in = torch.from_numpy(np.ascontiguousarray(host_np)).pin_memory()
+        host_out = torch.empty_like(host_in).pin_memory()
+        frames = max(1, K // CHUNK)
+        with torch.cuda.stream(stream):
+            g = Integrator(p.psi0, p.h, p.a, p.s, p.V, "msd", p.order, args.dtype, device=dev, stream=stream)
+            dev_psi = g.psi
+            g.step(Wm, dt)
+            g.sync()
+            barrier()
+            w0 = time.perf_counter()
+            for _ in range(frames):
+                dev_psi.copy_(host_in, non_blocking=True)
+                g.step(CHUNK, dt)
+                host_out.copy_(dev_psi, non_blocking=True)
+                g.mass()          # synchronises the stream: the frame's result is on the host
+            wall = time.perf_counter() - w0
+            barrier()
+        t = torch.tensor([wall], dtype=torch.float64, device=dev)
+        if dist is not None:
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        if rank == 0:
+            e2e_v = world * sites * CHUNK * frames / float(t.item()) / 1e9
+            nbytes = host_in.numel() * host_in.element_size()
+            result["e2e"] = {"value": round(e2e_v, 4), "unit": UNIT,
+                             "h2d_bytes_per_step": nbytes // CHUNK, "d2h_bytes_per_step": (nbytes + 8) // CHUNK,
+                             "chunk_steps": CHUNK, "frames": frames}
+
+    # ---- CPU baseline: the oracle on a bounded sample of the same workload ----
+    if rank == 0 and not args.no_cpu_baseline:
+        result["cpu_baseline"] = cpu_baseline(p, dt, budget_s=args.cpu_budget)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    return result
+
+
+def cpu_baseline(p, dt, budget_s=20.0, steps=None):
+    """The oracle as it stands, on all host cores, on a z-slab of the workload."""
+    import oracle
+    cores = oracle.set_threads(os.cpu_count() or 1)
+    # size the slab so that the run takes about budget_s seconds (first a probe)
+    nz_probe = min(p.shape[0], 16)
+    sl = p.psi0[:nz_probe]
+    Vs = p.V[:nz_probe] if p.V is not None else None
+    t0 = time.perf_counter()
+    oracle.rk4(sl, p.h, p.a, p.s, dt, 1, Vs, p.bc, p.order)
+    t_probe = time.perf_counter() - t0
+    per_site = t_probe / sl.size
+    nsteps = steps or 2
+    nz = int(max(5, min(p.shape[0], budget_s / (per_site * nsteps * sl[0].size))))
+    sl = np.ascontiguousarray(p.psi0[:nz])
+    Vs = np.ascontiguousarray(p.V[:nz]) if p.V is not None else None
+    t0 = time.perf_counter()
+    oracle.rk4(sl, p.h, p.a, p.s, dt, nsteps, Vs, p.bc, p.order)
+    el = time.perf_counter() - t0
+    v = sl.size * nsteps / el / 1e9
+    return {"value": round(v, 6), "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{nsteps} RK4 steps on a {nz}x{p.shape[1]}x{p.shape[2]} slab of the workload "
+                      f"({el:.1f} s, FP64, {platform.machine()})"}
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the oracle (plain FP64 CPU program) on the same metric
+# ---------------------------------------------------------------------------
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    import oracle
+    p = build_problem(args.workload)
+    s_rho = abs(p.s) * float(np.max(np.abs(p.psi0))) ** 2
+    dt = 0.8 * oracle.stability_bound(3, p.h, p.a, p.order, p.vmax(), s_rho)
+    cores = oracle.set_threads(os.cpu_count() or 1)
+    # one bench step = one RK4 step on a z-slab sized to ~budget / (K + W) seconds
+    per_step_budget = max(0.5, args.ref_budget / max(1, args.steps + args.warmup))
+    probe = np.ascontiguousarray(p.psi0[:8])
+    Vp = np.ascontiguousarray(p.V[:8])
+    t0 = time.perf_counter()
+    oracle.rk4(probe, p.h, p.a, p.s, dt, 1, Vp, p.bc, p.order)
+    per_plane = (time.perf_counter() - t0) / 8
+    nz = int(max(5, min(p.shape[0], per_step_budget / per_plane)))
+    psi = np.ascontiguousarray(p.psi0[:nz])
+    V = np.ascontiguousarray(p.V[:nz])
+    psi = oracle.rk4(psi, p.h, p.a, p.s, dt, args.warmup, V, p.bc, p.order)
+    t0 = time.perf_counter()
+    oracle.rk4(psi, p.h, p.a, p.s, dt, args.steps, V, p.bc, p.order)
+    el = time.perf_counter() - t0
+    v = psi.size * args.steps / el / 1e9
+    sample = f"{args.steps} RK4 steps on a {nz}x{p.shape[1]}x{p.shape[2]} slab of the workload"
+    return {"impl": "reference", "metric": METRIC, "value": round(v, 6), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(el / args.steps * 1e3, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded trap-vortex IC, no dataset)",
+            "config": {"workload": args.workload, "grid": list(p.shape), "order": p.order, "bc": "msd",
+                       "dt": dt, "precision": "c128"},
+            "cpu_baseline": {"value": round(v, 6), "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": round(v, 6), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="trap_vortex_3d_256x256x512")
+    ap.add_argument("--dtype", choices=["c128", "c64", "c64_acc64"], default="c128")
+    ap.add_argument("--no-forms", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--ref-budget", type=float, default=90.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local_rank = int(os.environ.get("LOCAL_RANK", 0))
+    if args.impl == "reference":
+        res = run_reference(args, rank, world)
+    else:
+        res = run_ours(args, rank, world, local_rank)
+    if rank == 0 and res is not None:
+        print(json.dumps(res), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,149 @@
+/*
+ * nlse.h -- C ABI of the GB300 (sm_103a) RK4 integrator for the nonlinear
+ * Schroedinger / Gross-Pitaevskii equation
+ *
+ *     i dPsi/dt + a Lap(Psi) - V(r) Psi + s |Psi|^2 Psi = 0          (Sec. 1, Eq. NLSE)
+ *
+ * on 1D, 2D and 3D complex grids with one spacing h on every axis (Sec. 3,
+ * Eq. disc), advanced by classic RK4 (Sec. 3.1, Eq. RK4) with F(Psi) =
+ * i[a Lap Psi + (s|Psi|^2 - V) Psi], the central-difference (order 2) or
+ * two-step compact 2SHOC (order 4) Laplacian (Sec. 3.2), and the Dirichlet
+ * or modulus-squared Dirichlet (MSD) boundary (Sec. 3.3).
+ *
+ * Conventions shared by every call
+ *   Layout     C order, last index fastest: a 3D grid is (N[0], N[1], N[2]) =
+ *              (Nz, Ny, Nx).  Boundary sites are those with any index 0 or
+ *              N[k]-1; the rest are interior.  Every N[k] >= 3.
+ *   Psi        interleaved complex: NLSE_C128 -> double2 (re, im),
+ *              NLSE_C64 -> float2, NLSE_C64_ACC64 -> double2 (the FP64 master).
+ *   V          real, same shape: double for NLSE_C128, float for the other two;
+ *              NULL means V = 0.
+ *   Pointers   psi, V and workspace are DEVICE pointers owned by the caller.
+ *              The library never allocates, frees or copies them; a context
+ *              borrows them until nlse_destroy.  Host pointers are named *_host.
+ *   Streams    stream is a cudaStream_t passed as void* (NULL = legacy default
+ *              stream).  nlse_step is asynchronous on that stream; nlse_mass,
+ *              nlse_energy and nlse_sync synchronise it.
+ *   Errors     every int-returning call returns NLSE_OK (0) or a negative
+ *              status below; nlse_last_error() gives a message for the last
+ *              failure on the calling thread.  A failed call changes nothing
+ *              unless its description says otherwise.
+ */
+#ifndef NLSE_H
+#define NLSE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---- */
+#define NLSE_OK          0
+#define NLSE_EINVAL     -1  /* bad argument (dims, N, h, a, order, bc, dtype, pointer, dt <= 0) */
+#define NLSE_ENOMEM     -2  /* the caller's workspace is smaller than nlse_workspace_bytes() */
+#define NLSE_ECUDA      -3  /* a CUDA launch or runtime call failed */
+#define NLSE_EUNSTABLE  -4  /* dt above the RK4 linear stability bound (see nlse_max_dt) */
+#define NLSE_ENONFINITE -5  /* a NaN or Inf appeared in Psi (sticky until the next nlse_create) */
+#define NLSE_ETIMEOUT   -6  /* a bounded device-side wait gave up */
+#define NLSE_ESTATE     -7  /* call not valid in the context's current state */
+
+/* ---- boundary conditions (Sec. 3.3) ---- */
+#define NLSE_BC_DIRICHLET 0 /* Eq. BCDdef: Psi_b is held at its value; Laplacian form Eq. BCDlap */
+#define NLSE_BC_MSD       1 /* Eq. BCMSDdef: |Psi_b|^2 held; Eq. msd and Eq. BCMSDlap */
+
+/* ---- precision forms ---- */
+#define NLSE_C128      0 /* FP64 throughout */
+#define NLSE_C64       1 /* FP32 throughout (the paper's single-precision codes, Sec. 5.2) */
+#define NLSE_C64_ACC64 2 /* FP32 stage arithmetic and stage arrays, FP64 master Psi and RK4
+                            accumulation (Psi^{n+1} = Psi^n + dt/6 (K_tot + k) in FP64),
+                            FP64 mass/energy reductions */
+
+typedef struct nlse_ctx *nlse_t;
+
+/*
+ * Bytes of device workspace a context needs (stage arrays K_tot, Psi_tmp,
+ * Psi_out of Eq. RK4_GPU in the dtype's stage precision, plus the FP32 copy
+ * of Psi^n for NLSE_C64_ACC64, reduction partials and status words).
+ * Returns 0 for invalid arguments.
+ */
+size_t nlse_workspace_bytes(int dims, const int64_t *N, int dtype);
+
+/*
+ * Create an integrator context over caller-owned device memory.
+ *   dims       1, 2 or 3;  N: host array of dims extents, each >= 3
+ *   h, a       grid spacing and dispersion coefficient, both > 0;  s: any real
+ *   V          device potential (see conventions) or NULL
+ *   bc, order  NLSE_BC_*, and 2 (central difference) or 4 (2SHOC)
+ *   psi        device Psi, read and written in place by nlse_step
+ *   workspace  device buffer of at least nlse_workspace_bytes(), 256-byte aligned
+ *   stream     cudaStream_t for every launch of this context
+ * Synchronises the stream once (it measures max|V| for the stability check).
+ * On success *out receives the context.
+ */
+int nlse_create(nlse_t *out, int dims, const int64_t *N, double h, double a, double s, const void *V, int bc,
+                int order, int dtype, void *psi, void *workspace, size_t ws_bytes, void *stream);
+
+/*
+ * Advance Psi by nsteps RK4 steps of size dt (Eq. RK4, computed as the four
+ * fused stages of Eq. RK4_GPU: each stage evaluates F with the boundary
+ * condition and applies its update in one pass).  Asynchronous on the
+ * context's stream.  nsteps == 0 is a no-op.  Fails with NLSE_EUNSTABLE when
+ * dt exceeds nlse_max_dt(dims, h, a, order, max|V|, 0), the linear bound
+ * without the 0.8 safety factor the paper's drivers apply.  Calling it twice
+ * with n1 and n2 steps gives bit-for-bit the result of one call with n1 + n2.
+ */
+int nlse_step(nlse_t ctx, int64_t nsteps, double dt);
+
+/*
+ * Mass  M = h^d sum_{all sites} |Psi|^2, in FP64 with compensated
+ * (Neumaier) summation and a deterministic two-pass reduction.  Synchronises
+ * the stream.  Returns NLSE_ENONFINITE if Psi holds a NaN or Inf.
+ */
+int nlse_mass(nlse_t ctx, double *out_host);
+
+/*
+ * Energy  E = h^d sum_{interior} [ -a Re(conj(Psi) Lap Psi) + V|Psi|^2 - (s/2)|Psi|^4 ]
+ * with the context's own Laplacian (order and boundary Laplacian form), in
+ * FP64.  The paper defines no energy; this is the discrete Hamiltonian of the
+ * semi-discrete flow.  Synchronises the stream.
+ */
+int nlse_energy(nlse_t ctx, double *out_host);
+
+/*
+ * F(Psi) = i[a Lap Psi + (s|Psi|^2 - V) Psi] at every site of an arbitrary
+ * state psi_in (same dtype, shape and device as the context's Psi; for
+ * NLSE_C64_ACC64 it is float2), written to F_out (same type).  Boundary sites
+ * get the boundary condition's time derivative (Eqs. BCDdt, msd).
+ * Asynchronous.  For testing the right-hand side on its own.
+ */
+int nlse_rhs(nlse_t ctx, const void *psi_in, void *F_out);
+
+/*
+ * RK4 linear stability bound on dt (Sec. 3.4): 2 sqrt(2) / (a rho_L + vmax +
+ * s_rho_max) with rho_L = 4d/h^2 (order 2) or 16d/(3h^2) (order 4).  With
+ * vmax = s_rho_max = 0 this is Eqs. stblincd / stblin2shoc.  Drivers usually
+ * take 0.8 of it.  Returns a negative value for invalid arguments.
+ */
+double nlse_max_dt(int dims, double h, double a, int order, double vmax, double s_rho_max);
+
+/* Wait for the context's stream and report a sticky non-finite flag or a
+ * CUDA error. */
+int nlse_sync(nlse_t ctx);
+
+/* Release the context (never the caller's device buffers). */
+int nlse_destroy(nlse_t ctx);
+
+/* Message for the last failed call on this thread ("" if none). */
+const char *nlse_last_error(void);
+
+/* Which stage kernel the context uses: 0 = generic one-thread-per-site
+ * kernel, 1 = tiled kernel (2D rows / 3D z-marching).  Set before nlse_step;
+ * the default is 1 where a tiled kernel exists. */
+int nlse_set_kernel(nlse_t ctx, int variant);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NLSE_H */

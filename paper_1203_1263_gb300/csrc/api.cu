@@ -1,0 +1,403 @@
+// The C ABI of include/nlse.h: argument checks, workspace layout, stage
+// dispatch, CUDA-graph chunking of the step loop, reductions and errors.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include "../../include/nlse.h"
+#include "nlse_internal.h"
+
+using namespace nlse;
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+int fail(int code, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* where) {
+  return fail(NLSE_ECUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+constexpr int kGraphSteps = 16;   // RK4 steps captured per graph replay
+constexpr size_t kAlign = 256;
+
+size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+struct Layout {
+  size_t ktot, ptmp, pout, pn32, partials, status, total;
+};
+
+bool layout_for(int dims, const int64_t* N, int dtype, Layout* L, int64_t* total_sites) {
+  if (dims < 1 || dims > 3 || !N) return false;
+  if (dtype < NLSE_C128 || dtype > NLSE_C64_ACC64) return false;
+  int64_t total = 1;
+  for (int k = 0; k < dims; ++k) {
+    if (N[k] < 3 || N[k] > (int64_t(1) << 30)) return false;
+    total *= N[k];
+    if (total > (int64_t(1) << 40)) return false;
+  }
+  const size_t es = (dtype == NLSE_C128) ? 16 : 8;
+  size_t off = 0;
+  L->ktot = off; off = align_up(off + es * total);
+  L->ptmp = off; off = align_up(off + es * total);
+  L->pout = off; off = align_up(off + es * total);
+  L->pn32 = off; if (dtype == NLSE_C64_ACC64) off = align_up(off + 8 * total);
+  L->partials = off; off = align_up(off + sizeof(double) * 2 * kMaxReduceBlocks);
+  L->status = off; off = align_up(off + 256);
+  L->total = off;
+  if (total_sites) *total_sites = total;
+  return true;
+}
+
+}  // namespace
+
+struct nlse_ctx {
+  int d;
+  int64_t n[3];
+  int64_t total;
+  double h, a, s;
+  int bc, order, dtype;
+  void* psi;
+  const void* V;
+  cudaStream_t stream;
+  char* ws;
+  Layout lay;
+  double vmax;
+  int variant, tile_cfg;
+  cudaStream_t cap;
+  cudaGraphExec_t exec;
+  double graph_dt;
+  int graph_variant;
+
+  void* at(size_t off) const { return ws + off; }
+  unsigned int* flag() const { return (unsigned int*)(ws + lay.status); }
+  unsigned long long* vbits() const { return (unsigned long long*)(ws + lay.status + 8); }
+  double* result() const { return (double*)(ws + lay.status + 64); }
+  double* partials() const { return (double*)(ws + lay.partials); }
+};
+
+namespace {
+
+template <class T>
+Field<T> make_field(const nlse_ctx* c, const void* in) {
+  using R = typename T::R;
+  Field<T> f;
+  memset(&f, 0, sizeof(f));
+  for (int k = 0; k < 3; ++k) { f.n[k] = 1; f.m[k] = 1; f.st[k] = 0; }
+  int64_t stride = 1;
+  for (int k = c->d - 1; k >= 0; --k) {
+    f.n[k] = int(c->n[k]);
+    f.m[k] = int(c->n[k] - 2);
+    f.st[k] = stride;
+    stride *= c->n[k];
+  }
+  f.ninterior = 1;
+  for (int k = 0; k < c->d; ++k) f.ninterior *= (c->n[k] - 2);
+  f.a = R(c->a);
+  f.s = R(c->s);
+  f.h2_over_a = R(c->h * c->h / c->a);
+  f.cL = R(c->order == 4 ? c->a / (12.0 * c->h * c->h) : c->a / (c->h * c->h));
+  f.tiny = R(sizeof(R) == 8 ? 1e-300 : 1e-30);
+  f.bc = c->bc;
+  f.V = (const typename T::VR*)c->V;
+  f.in = (const typename T::C*)in;
+  return f;
+}
+
+template <class T>
+cudaError_t dispatch_stage(const nlse_ctx* c, const StageArgs<T>& A, cudaStream_t st) {
+  const int v = c->variant, t = c->tile_cfg;
+  switch (c->d * 10 + c->order) {
+    case 12: return launch_stage<T, 1, 2>(A, v, t, st);
+    case 14: return launch_stage<T, 1, 4>(A, v, t, st);
+    case 22: return launch_stage<T, 2, 2>(A, v, t, st);
+    case 24: return launch_stage<T, 2, 4>(A, v, t, st);
+    case 32: return launch_stage<T, 3, 2>(A, v, t, st);
+    default: return launch_stage<T, 3, 4>(A, v, t, st);
+  }
+}
+
+// One RK4 step = four fused stages (Eq. RK4_GPU): Psi -> Psi_tmp -> Psi_out -> Psi_tmp -> Psi.
+template <class T>
+cudaError_t launch_step(const nlse_ctx* c, double dt, cudaStream_t st) {
+  using C = typename T::C;
+  using R = typename T::R;
+  const bool mix = (c->dtype == NLSE_C64_ACC64);
+  C* ktot = (C*)c->at(c->lay.ktot);
+  C* ptmp = (C*)c->at(c->lay.ptmp);
+  C* pout = (C*)c->at(c->lay.pout);
+  const C* psin = mix ? (const C*)c->at(c->lay.pn32) : (const C*)c->psi;
+  const void* in[4] = {psin, ptmp, pout, ptmp};
+  C* outs[4] = {ptmp, pout, ptmp, nullptr};
+  const double dtc[4] = {dt / 2.0, dt / 2.0, dt, dt / 6.0};
+  for (int s = 0; s < 4; ++s) {
+    StageArgs<T> A;
+    memset(&A, 0, sizeof(A));
+    A.f = make_field<T>(c, in[s]);
+    A.psin = psin;
+    A.ktot = ktot;
+    A.out = outs[s];
+    A.master = (typename T::M*)c->psi;
+    A.n32 = mix ? (C*)c->at(c->lay.pn32) : nullptr;
+    A.dtc = R(dtc[s]);
+    A.dt6 = dt / 6.0;
+    A.stage = s + 1;
+    A.flag = c->flag();
+    cudaError_t e = dispatch_stage<T>(c, A, st);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t launch_step_any(const nlse_ctx* c, double dt, cudaStream_t st) {
+  switch (c->dtype) {
+    case NLSE_C128: return launch_step<P64>(c, dt, st);
+    case NLSE_C64: return launch_step<P32>(c, dt, st);
+    default: return launch_step<PMix>(c, dt, st);
+  }
+}
+
+void drop_graph(nlse_ctx* c) {
+  if (c->exec) cudaGraphExecDestroy(c->exec);
+  c->exec = nullptr;
+}
+
+int ensure_graph(nlse_ctx* c, double dt) {
+  if (c->exec && c->graph_dt == dt && c->graph_variant == c->variant) return NLSE_OK;
+  drop_graph(c);
+  if (!c->cap) {
+    cudaError_t e = cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamCreate");
+  }
+  cudaError_t e = cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamBeginCapture");
+  cudaError_t le = cudaSuccess;
+  for (int i = 0; i < kGraphSteps && le == cudaSuccess; ++i) le = launch_step_any(c, dt, c->cap);
+  cudaGraph_t g = nullptr;
+  e = cudaStreamEndCapture(c->cap, &g);
+  if (le != cudaSuccess) { if (g) cudaGraphDestroy(g); return cuda_fail(le, "stage launch (capture)"); }
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+  e = cudaGraphInstantiate(&c->exec, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) { c->exec = nullptr; return cuda_fail(e, "cudaGraphInstantiate"); }
+  c->graph_dt = dt;
+  c->graph_variant = c->variant;
+  return NLSE_OK;
+}
+
+__global__ void k_round_master(const double2* __restrict__ m, float2* __restrict__ o, int64_t total) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const double2 v = m[i];
+    o[i] = make_float2(float(v.x), float(v.y));
+  }
+}
+
+int read_status(nlse_ctx* c) {
+  unsigned int flag = 0;
+  cudaError_t e = cudaMemcpyAsync(&flag, c->flag(), sizeof(flag), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "status read");
+  if (flag & 3u) return fail(NLSE_ENONFINITE, "non-finite value in Psi");
+  return NLSE_OK;
+}
+
+}  // namespace
+
+namespace nlse {
+cudaError_t launch_round_master(const double2* master, float2* n32, int64_t total, cudaStream_t stream) {
+  int64_t b = (total + 255) / 256;
+  if (b > 152 * 16) b = 152 * 16;
+  k_round_master<<<(unsigned)b, 256, 0, stream>>>(master, n32, total);
+  return cudaGetLastError();
+}
+}  // namespace nlse
+
+extern "C" {
+
+const char* nlse_last_error(void) { return g_err; }
+
+size_t nlse_workspace_bytes(int dims, const int64_t* N, int dtype) {
+  Layout L;
+  if (!layout_for(dims, N, dtype, &L, nullptr)) return 0;
+  return L.total;
+}
+
+double nlse_max_dt(int dims, double h, double a, int order, double vmax, double s_rho_max) {
+  if (dims < 1 || dims > 3 || !(h > 0) || !(a > 0) || (order != 2 && order != 4)) return -1.0;
+  // spectral radius of Lap on the grid: 4d/h^2 (CD), 16d/(3h^2) (2SHOC); RK4 reaches 2 sqrt(2) on i R
+  const double rho = (order == 4 ? 16.0 * dims / 3.0 : 4.0 * dims) / (h * h);
+  return 2.0 * sqrt(2.0) / (a * rho + fabs(vmax) + fabs(s_rho_max));
+}
+
+int nlse_create(nlse_t* out, int dims, const int64_t* N, double h, double a, double s, const void* V, int bc,
+                int order, int dtype, void* psi, void* workspace, size_t ws_bytes, void* stream) {
+  g_err[0] = 0;
+  if (!out) return fail(NLSE_EINVAL, "out is NULL");
+  *out = nullptr;
+  Layout L;
+  int64_t total = 0;
+  if (!layout_for(dims, N, dtype, &L, &total))
+    return fail(NLSE_EINVAL, "bad dims/N/dtype (dims in 1..3, every N >= 3, dtype 0..2)");
+  if (!(h > 0) || !isfinite(h)) return fail(NLSE_EINVAL, "h must be > 0");
+  if (!(a > 0) || !isfinite(a)) return fail(NLSE_EINVAL, "a must be > 0");
+  if (!isfinite(s)) return fail(NLSE_EINVAL, "s must be finite");
+  if (bc != NLSE_BC_DIRICHLET && bc != NLSE_BC_MSD) return fail(NLSE_EINVAL, "bc must be 0 or 1");
+  if (order != 2 && order != 4) return fail(NLSE_EINVAL, "order must be 2 or 4");
+  if (!psi) return fail(NLSE_EINVAL, "psi is NULL");
+  if (!workspace) return fail(NLSE_EINVAL, "workspace is NULL");
+  if ((uintptr_t)workspace % kAlign) return fail(NLSE_EINVAL, "workspace must be 256-byte aligned");
+  if ((uintptr_t)psi % 16 || (V && (uintptr_t)V % 8)) return fail(NLSE_EINVAL, "psi/V misaligned");
+  if (ws_bytes < L.total) return fail(NLSE_ENOMEM, "workspace %zu bytes < %zu needed", ws_bytes, L.total);
+
+  nlse_ctx* c = new nlse_ctx();
+  memset(c, 0, sizeof(*c));
+  c->d = dims;
+  for (int k = 0; k < 3; ++k) c->n[k] = (k < dims) ? N[k] : 1;
+  c->total = total;
+  c->h = h; c->a = a; c->s = s;
+  c->bc = bc; c->order = order; c->dtype = dtype;
+  c->psi = psi; c->V = V;
+  c->stream = (cudaStream_t)stream;
+  c->ws = (char*)workspace;
+  c->lay = L;
+  c->variant = 1;
+  c->tile_cfg = -1;
+  c->graph_dt = -1.0;
+
+  cudaError_t e = cudaMemsetAsync(c->at(L.status), 0, 256, c->stream);
+  if (e == cudaSuccess && V) {
+    e = launch_vmax(V, dtype == NLSE_C128, total, c->vbits(), c->stream);
+    unsigned long long bits = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&bits, c->vbits(), sizeof(bits), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    memcpy(&c->vmax, &bits, sizeof(double));
+  }
+  if (e != cudaSuccess) {
+    delete c;
+    return cuda_fail(e, "nlse_create");
+  }
+  *out = c;
+  return NLSE_OK;
+}
+
+int nlse_set_kernel(nlse_t c, int variant) {
+  if (!c) return fail(NLSE_EINVAL, "NULL context");
+  if (variant < 0 || variant > 1) return fail(NLSE_EINVAL, "variant must be 0 or 1");
+  c->variant = variant;
+  drop_graph(c);
+  return NLSE_OK;
+}
+
+int nlse_step(nlse_t c, int64_t nsteps, double dt) {
+  if (!c) return fail(NLSE_EINVAL, "NULL context");
+  if (nsteps < 0) return fail(NLSE_EINVAL, "nsteps < 0");
+  if (!(dt > 0) || !isfinite(dt)) return fail(NLSE_EINVAL, "dt must be > 0");
+  const double bound = nlse_max_dt(c->d, c->h, c->a, c->order, c->vmax, 0.0);
+  if (dt > bound) return fail(NLSE_EUNSTABLE, "dt = %g above the RK4 linear stability bound %g", dt, bound);
+  if (nsteps == 0) return NLSE_OK;
+  cudaError_t e = cudaSuccess;
+  if (c->dtype == NLSE_C64_ACC64)
+    e = launch_round_master((const double2*)c->psi, (float2*)c->at(c->lay.pn32), c->total, c->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "round master");
+  int64_t left = nsteps;
+  if (nsteps >= kGraphSteps) {
+    int rc = ensure_graph(c, dt);
+    if (rc != NLSE_OK) return rc;
+    for (; left >= kGraphSteps; left -= kGraphSteps) {
+      e = cudaGraphLaunch(c->exec, c->stream);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
+    }
+  }
+  for (; left > 0; --left) {
+    e = launch_step_any(c, dt, c->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "stage launch");
+  }
+  return NLSE_OK;
+}
+
+int nlse_rhs(nlse_t c, const void* psi_in, void* F_out) {
+  if (!c || !psi_in || !F_out) return fail(NLSE_EINVAL, "NULL argument");
+  cudaError_t e;
+  auto run = [&](auto tag) {
+    using T = decltype(tag);
+    StageArgs<T> A;
+    memset(&A, 0, sizeof(A));
+    A.f = make_field<T>(c, psi_in);
+    A.out = (typename T::C*)F_out;
+    A.stage = 0;
+    A.flag = c->flag();
+    return dispatch_stage<T>(c, A, c->stream);
+  };
+  if (c->dtype == NLSE_C128) e = run(P64{});
+  else if (c->dtype == NLSE_C64) e = run(P32{});
+  else e = run(PMix{});
+  if (e != cudaSuccess) return cuda_fail(e, "rhs launch");
+  return NLSE_OK;
+}
+
+int nlse_mass(nlse_t c, double* out_host) {
+  if (!c || !out_host) return fail(NLSE_EINVAL, "NULL argument");
+  cudaError_t e = launch_mass(c->psi, c->dtype != NLSE_C64, c->total, pow(c->h, c->d), c->partials(), c->result(),
+                              c->flag(), c->stream);
+  double v = 0.0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&v, c->result(), sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "mass");
+  int rc = read_status(c);
+  if (rc != NLSE_OK) return rc;
+  *out_host = v;
+  return NLSE_OK;
+}
+
+int nlse_energy(nlse_t c, double* out_host) {
+  if (!c || !out_host) return fail(NLSE_EINVAL, "NULL argument");
+  const double scale = pow(c->h, c->d);
+  cudaError_t e;
+  auto run = [&](auto tag) {
+    using T = decltype(tag);
+    Field<T> f = make_field<T>(c, c->psi);
+    switch (c->d * 10 + c->order) {
+      case 12: return launch_energy<T, 1, 2>(f, scale, c->partials(), c->result(), c->flag(), c->stream);
+      case 14: return launch_energy<T, 1, 4>(f, scale, c->partials(), c->result(), c->flag(), c->stream);
+      case 22: return launch_energy<T, 2, 2>(f, scale, c->partials(), c->result(), c->flag(), c->stream);
+      case 24: return launch_energy<T, 2, 4>(f, scale, c->partials(), c->result(), c->flag(), c->stream);
+      case 32: return launch_energy<T, 3, 2>(f, scale, c->partials(), c->result(), c->flag(), c->stream);
+      default: return launch_energy<T, 3, 4>(f, scale, c->partials(), c->result(), c->flag(), c->stream);
+    }
+  };
+  if (c->dtype == NLSE_C128) e = run(P64{});
+  else if (c->dtype == NLSE_C64) e = run(E32{});
+  else e = run(EMix{});
+  double v = 0.0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&v, c->result(), sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "energy");
+  int rc = read_status(c);
+  if (rc != NLSE_OK) return rc;
+  *out_host = v;
+  return NLSE_OK;
+}
+
+int nlse_sync(nlse_t c) {
+  if (!c) return fail(NLSE_EINVAL, "NULL context");
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "pending error");
+  return read_status(c);
+}
+
+int nlse_destroy(nlse_t c) {
+  if (!c) return NLSE_OK;
+  drop_graph(c);
+  if (c->cap) cudaStreamDestroy(c->cap);
+  delete c;
+  return NLSE_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,20 @@
+// Launchers shared between the library's translation units (not exported).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "nlse_device.cuh"
+
+namespace nlse {
+
+constexpr int kMaxReduceBlocks = 1024;
+
+cudaError_t launch_mass(const void* psi, bool psi_double, int64_t total, double scale, double* partials,
+                        double* result, unsigned int* flag, cudaStream_t stream);
+template <class T, int D, int ORDER>
+cudaError_t launch_energy(const Field<T>& f, double scale, double* partials, double* result, unsigned int* flag,
+                          cudaStream_t stream);
+cudaError_t launch_vmax(const void* V, bool v_double, int64_t total, unsigned long long* out, cudaStream_t stream);
+cudaError_t launch_round_master(const double2* master, float2* n32, int64_t total, cudaStream_t stream);
+
+}  // namespace nlse

@@ -1,0 +1,202 @@
+"""CUDA path vs the CPU oracle on seeded inputs, element by element.
+
+Tolerances (the end-time bars of the method, applied to every comparison):
+  FP64 (c128):            relative L2 <= 1e-12, max |diff| <= 1e-11 max|ref|
+  FP32 (c64, c64_acc64):  relative L2 <= 2e-5,  max |diff| <= 2e-4 max|ref|
+FP32 runs start from the FP64 inputs rounded to FP32 and are compared with
+the FP64 oracle.  Grid shapes span several tiles of the tiled kernels with
+ragged tails, and include the degenerate extents 3 and 4.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_1203_1263_gb300 import workloads as W
+from paper_1203_1263_gb300 import _lib as L
+from paper_1203_1263_gb300.integrator import Integrator
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"c128": (1e-12, 1e-11), "c64": (2e-5, 2e-4), "c64_acc64": (2e-5, 2e-4)}
+BCS = {"dirichlet": W.BC_DIRICHLET, "msd": W.BC_MSD}
+
+SHAPES = {
+    1: [(37,), (3,), (4,), (1000,)],
+    2: [(19, 45), (3, 7), (4, 40), (70, 33)],
+    3: [(9, 21, 70), (3, 4, 5), (13, 10, 37), (20, 17, 64)],
+}
+
+
+def _smooth(z, passes):
+    for _ in range(passes):
+        acc = z.copy()
+        for ax in range(z.ndim):
+            acc += np.roll(z, 1, ax) + np.roll(z, -1, ax)
+        z = acc / (2 * z.ndim + 1)
+    return z
+
+
+def field(shape, seed):
+    """Unit background with seeded, smoothed structure: density bumps of up to
+    +-30 % that vanish at the walls, and a smooth phase of amplitude 1.
+    MSD holds |Psi|^2 at the walls, which suits a near-constant background
+    (the paper's use of it); on a rough random field the wall-adjacent density
+    collapses and the wall ratio Im(F/Psi) blows up in the oracle as well."""
+    r = _smooth(W.random_field(shape, seed), 3)
+    r = r / np.max(np.abs(r))
+    win = np.ones(shape)
+    for ax, n in enumerate(shape):
+        sh = [1] * len(shape)
+        sh[ax] = n
+        win = win * (np.sin(np.pi * np.arange(n) / (n - 1)) ** 2).reshape(sh)
+    return ((1 + 0.3 * win * r.real) * np.exp(1j * r.imag)).astype(np.complex128)
+
+
+def compare(got, ref, dtype):
+    rl2, elem = TOL[dtype]
+    got = np.asarray(got, dtype=np.complex128)
+    err = np.linalg.norm((got - ref).ravel()) / np.linalg.norm(ref.ravel())
+    emax = np.max(np.abs(got - ref)) / np.max(np.abs(ref))
+    assert err <= rl2 and emax <= elem, (err, emax)
+    return err
+
+
+def problem(shape, seed, with_v=True):
+    psi = field(shape, seed)
+    V = W.random_potential(shape, seed + 1, 0.5) if with_v else None
+    return psi, V
+
+
+def stable_dt(shape, h, a, s, order, V, frac=0.2):
+    return frac * O.stability_bound(len(shape), h, a, order, 0.0 if V is None else float(np.max(V)), abs(s) * 1.7)
+
+
+CASES = [(d, shp) for d in (1, 2, 3) for shp in SHAPES[d]]
+_ORACLE_CACHE = {}
+
+
+def oracle_rk4_cached(key, *args):
+    if key not in _ORACLE_CACHE:
+        _ORACLE_CACHE[key] = O.rk4(*args)
+    return _ORACLE_CACHE[key]
+
+
+@pytest.mark.parametrize("dims,shape", CASES)
+@pytest.mark.parametrize("order", [2, 4])
+@pytest.mark.parametrize("bc", ["dirichlet", "msd"])
+@pytest.mark.parametrize("dtype", ["c128", "c64", "c64_acc64"])
+@pytest.mark.parametrize("variant", [0, 1])
+def test_step_matches_oracle(dims, shape, order, bc, dtype, variant):
+    h, a, s = 0.35, 0.8, -1.1
+    psi, V = problem(shape, 100 + dims * 10 + order)
+    dt = stable_dt(shape, h, a, s, order, V)
+    nsteps = 21   # one graph replay of 16 steps + 5 single steps
+    ref = oracle_rk4_cached((shape, order, bc), psi, h, a, s, dt, nsteps, V, BCS[bc], order)
+    g = Integrator(psi, h, a, s, V, bc, order, dtype)
+    g.set_kernel(variant)
+    g.step(nsteps, dt)
+    g.sync()
+    compare(g.numpy(), ref, dtype)
+
+
+@pytest.mark.parametrize("dims,shape", [(1, (37,)), (2, (19, 45)), (3, (9, 21, 70)), (3, (3, 4, 5))])
+@pytest.mark.parametrize("order", [2, 4])
+@pytest.mark.parametrize("bc", ["dirichlet", "msd"])
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_rhs_matches_oracle(dims, shape, order, bc, dtype):
+    h, a, s = 0.3, 0.9, 1.3
+    psi, V = problem(shape, 7 + dims)
+    ref = O.evalF(psi, h, a, s, V, BCS[bc], order)
+    g = Integrator(psi, h, a, s, V, bc, order, dtype)
+    got = g.rhs().cpu().numpy()
+    tol = 1e-13 if dtype == "c128" else 1e-5
+    assert np.max(np.abs(got - ref)) <= tol * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("dims,shape", [(1, (1000,)), (2, (70, 33)), (3, (20, 17, 64))])
+@pytest.mark.parametrize("order", [2, 4])
+@pytest.mark.parametrize("bc", ["dirichlet", "msd"])
+@pytest.mark.parametrize("dtype", ["c128", "c64", "c64_acc64"])
+def test_mass_energy_match_oracle(dims, shape, order, bc, dtype):
+    h, a, s = 0.25, 0.7, -0.6
+    psi, V = problem(shape, 55)
+    g = Integrator(psi, h, a, s, V, bc, order, dtype)
+    # the oracle sees exactly what the GPU holds (FP32 forms: the rounded state and potential)
+    held = g.numpy().astype(np.complex128)
+    Vh = V.astype(np.float32).astype(np.float64) if dtype != "c128" else V
+    m_ref = O.mass(held, h)
+    e_ref = O.energy(held, h, a, s, Vh, BCS[bc], order)
+    assert abs(g.mass() - m_ref) <= 1e-13 * abs(m_ref)
+    assert abs(g.energy() - e_ref) <= 1e-12 * abs(e_ref)
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64", "c64_acc64"])
+@pytest.mark.parametrize("variant", [0, 1])
+def test_split_continuation_and_determinism_bitwise(dtype, variant):
+    psi, V = problem((11, 12, 40), 3)
+    h, a, s, order = 0.3, 0.6, 1.0, 4
+    dt = stable_dt(psi.shape, h, a, s, order, V)
+    outs = []
+    for split in ([7, 13], [20], [3, 17]):
+        g = Integrator(psi, h, a, s, V, "msd", order, dtype)
+        g.set_kernel(variant)
+        for n in split:
+            g.step(n, dt)
+        outs.append(g.numpy())
+    assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[1], outs[2])
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64", "c64_acc64"])
+@pytest.mark.parametrize("dims,shape", [(2, (19, 45)), (3, (9, 21, 70)), (3, (20, 17, 64))])
+def test_tiled_kernel_equals_generic_bitwise(dtype, dims, shape):
+    """The tiled kernels perform the generic kernel's arithmetic in the same
+    order; only where the operands come from differs."""
+    for order in (2, 4):
+        for bc in ("dirichlet", "msd"):
+            psi, V = problem(shape, 77)
+            h, a, s = 0.3, 0.6, -1.0
+            dt = stable_dt(shape, h, a, s, order, V)
+            res = []
+            for variant in (0, 1):
+                g = Integrator(psi, h, a, s, V, bc, order, dtype)
+                g.set_kernel(variant)
+                g.step(5, dt)
+                res.append(g.numpy())
+            assert np.array_equal(res[0], res[1]), (order, bc)
+
+
+def test_dt_above_bound_is_rejected():
+    psi, V = problem((10, 10), 4)
+    g = Integrator(psi, 0.2, 1.0, 1.0, V, "dirichlet", 4, "c128")
+    bound = g.max_dt()
+    with pytest.raises(L.NLSEError) as e:
+        g.step(1, bound * 1.01)
+    assert e.value.code == L.NLSE_EUNSTABLE
+    g.step(1, bound * 0.99)
+    g.sync()
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64", "c64_acc64"])
+def test_non_finite_is_reported(dtype):
+    psi, V = problem((8, 9, 10), 5)
+    psi[4, 4, 4] = np.nan
+    g = Integrator(psi, 0.3, 1.0, 1.0, V, "msd", 4, dtype)
+    g.step(2, 1e-4)
+    with pytest.raises(L.NLSEError) as e:
+        g.sync()
+    assert e.value.code == L.NLSE_ENONFINITE
+    with pytest.raises(L.NLSEError):
+        g.mass()
+
+
+def test_zero_steps_and_bad_dt():
+    psi, V = problem((6, 7), 6)
+    g = Integrator(psi, 0.3, 1.0, 1.0, V, "msd", 2, "c128")
+    before = g.numpy()
+    g.step(0, 1e-3)
+    assert np.array_equal(before, g.numpy())
+    for bad in (0.0, -1e-3, float("nan")):
+        with pytest.raises(L.NLSEError) as e:
+            g.step(1, bad)
+        assert e.value.code == L.NLSE_EINVAL
