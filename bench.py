@@ -37,6 +37,7 @@ from paper_1203_1263_gb300 import workloads as W  # noqa: E402
 WORKLOADS = {
     "trap_vortex_3d_256x256x512": dict(shape=(512, 256, 256)),
     "trap_vortex_3d_87x87x203": dict(shape=(203, 87, 87)),
+    "trap_vortex_3d_256x256x256": dict(shape=(256, 256, 256)),
 }
 METRIC = "RK4 site-updates/s (Gsite*step/s)"
 UNIT = "Gsite*step/s"
@@ -141,6 +142,7 @@ def run_ours(args, rank, world, local_rank):
     def timed(dtype, K, Wm):
         with torch.cuda.stream(stream):
             g = Integrator(p.psi0, p.h, p.a, p.s, p.V, "msd", p.order, dtype, device=dev, stream=stream)
+            g.set_kernel(args.variant, args.tile)
             g.step(Wm, dt)
             g.sync()
             barrier()
@@ -218,6 +220,7 @@ def run_ours(args, rank, world, local_rank):
         frames = max(1, K // CHUNK)
         with torch.cuda.stream(stream):
             g = Integrator(p.psi0, p.h, p.a, p.s, p.V, "msd", p.order, args.dtype, device=dev, stream=stream)
+            g.set_kernel(args.variant, args.tile)
             dev_psi = g.psi
             g.step(Wm, dt)
             g.sync()
@@ -320,6 +323,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="trap_vortex_3d_256x256x512")
     ap.add_argument("--dtype", choices=["c128", "c64", "c64_acc64"], default="c128")
+    ap.add_argument("--variant", type=int, default=1, help="stage kernel: 0 generic, 1 tiled")
+    ap.add_argument("--tile", type=int, default=-1, help="tiled kernel CTA shape (-1 default)")
     ap.add_argument("--no-forms", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -138,10 +138,37 @@ int nlse_destroy(nlse_t ctx);
 /* Message for the last failed call on this thread ("" if none). */
 const char *nlse_last_error(void);
 
-/* Which stage kernel the context uses: 0 = generic one-thread-per-site
- * kernel, 1 = tiled kernel (2D rows / 3D z-marching).  Set before nlse_step;
- * the default is 1 where a tiled kernel exists. */
-int nlse_set_kernel(nlse_t ctx, int variant);
+/* Which stage kernel the context uses:
+ *   0 = generic one-thread-per-site kernel,
+ *   1 = tiled kernel (2D halo tiles / 3D z-marching; 1D grids always use the
+ *       generic kernel),
+ *   2 = tiled kernel with the exact-sum stencil (NLSE_C128 only; other
+ *       dtypes treat it as 1): the Laplacian's stencil sums are formed exactly
+ *       in 64-bit fixed point on the integer pipe and converted to FP64 once,
+ *   3 = generic kernel with the exact-sum stencil (NLSE_C128; else as 0).
+ * Variants 0 and 1 give bit-for-bit the same result, and so do 2 and 3.
+ * tile_cfg picks the tiled kernel's CTA tile (x-by-y threads): 0 = 32x8,
+ * 1 = 64x4, 2 = 32x16, 3 = 64x8, -1 = default; it never changes results.
+ * Call between nlse_step calls, not during one. */
+int nlse_set_kernel(nlse_t ctx, int variant, int tile_cfg);
+
+/*
+ * Test hooks for the bounded device-side waits (not needed in normal use).
+ *   NLSE_DEBUG_SPIN_LIMIT  value = SM clock cycles any device-side wait may
+ *                          last before the kernel gives up (default ~2e9,
+ *                          about a second).
+ *   NLSE_DEBUG_EXTRA_TX    value = extra bytes (multiple of 16, <= 2^20) that
+ *                          every TMA barrier of the 3D tiled kernel expects
+ *                          beyond what its copy delivers, so its wait runs out
+ *                          without any fault; the next nlse_sync then returns
+ *                          NLSE_ETIMEOUT once.  0 restores normal operation.
+ * Psi is not valid after a step that timed out; reporting NLSE_ETIMEOUT
+ * clears every status flag (including a non-finite flag the invalid step
+ * may have raised), and the context stays usable once Psi is restored.
+ */
+#define NLSE_DEBUG_SPIN_LIMIT 1
+#define NLSE_DEBUG_EXTRA_TX   2
+int nlse_debug_set(nlse_t ctx, int key, long long value);
 
 #ifdef __cplusplus
 }

@@ -25,6 +25,8 @@ BC_MSD = 1
 C128 = 0
 C64 = 1
 C64_ACC64 = 2
+DEBUG_SPIN_LIMIT = 1
+DEBUG_EXTRA_TX = 2
 
 STATUS_NAMES = {0: "NLSE_OK", -1: "NLSE_EINVAL", -2: "NLSE_ENOMEM", -3: "NLSE_ECUDA", -4: "NLSE_EUNSTABLE",
                 -5: "NLSE_ENONFINITE", -6: "NLSE_ETIMEOUT", -7: "NLSE_ESTATE"}
@@ -46,7 +48,8 @@ SIGNATURES = {
     "nlse_sync": (_I, [_VP]),
     "nlse_destroy": (_I, [_VP]),
     "nlse_last_error": (ctypes.c_char_p, []),
-    "nlse_set_kernel": (_I, [_VP, _I]),
+    "nlse_set_kernel": (_I, [_VP, _I, _I]),
+    "nlse_debug_set": (_I, [_VP, _I, ctypes.c_longlong]),
 }
 
 

@@ -1,5 +1,6 @@
 // The C ABI of include/nlse.h: argument checks, workspace layout, stage
 // dispatch, CUDA-graph chunking of the step loop, reductions and errors.
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdarg.h>
@@ -28,6 +29,28 @@ int cuda_fail(cudaError_t e, const char* where) {
 }
 
 constexpr int kGraphSteps = 16;   // RK4 steps captured per graph replay
+constexpr long long kSpinLimit = 2000000000ll;   // ~1 s of SM clock: bound on device-side waits
+constexpr unsigned int kFlagTimeoutBit = 4u;
+
+// cuTensorMapEncodeTiled, resolved once through the runtime (no link to libcuda).
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+    else
+      cudaGetLastError();
+  }
+  return fn;
+}
 constexpr size_t kAlign = 256;
 
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
@@ -72,11 +95,17 @@ struct nlse_ctx {
   char* ws;
   Layout lay;
   double vmax;
+  int fixF;          // fraction bits of the exact-sum stencil (FP64 path)
   int variant, tile_cfg;
   cudaStream_t cap;
   cudaGraphExec_t exec;
   double graph_dt;
   int graph_variant;
+  // TMA descriptors of the stage inputs (Psi or its FP32 copy, Psi_tmp, Psi_out) per tile shape
+  CUtensorMap tmaps[4][3];
+  signed char tmap_state[4][3];   // 0 = not built, 1 = ok, -1 = layout not eligible
+  long long spin_limit;           // bound on device-side waits (cycles)
+  unsigned int extra_tx;          // test hook, see nlse_debug_set
 
   void* at(size_t off) const { return ws + off; }
   unsigned int* flag() const { return (unsigned int*)(ws + lay.status); }
@@ -108,22 +137,58 @@ Field<T> make_field(const nlse_ctx* c, const void* in) {
   f.cL = R(c->order == 4 ? c->a / (12.0 * c->h * c->h) : c->a / (c->h * c->h));
   f.tiny = R(sizeof(R) == 8 ? 1e-300 : 1e-30);
   f.bc = c->bc;
+  f.F = c->fixF;
+  f.cLF = ldexp(c->order == 4 ? c->a / (12.0 * c->h * c->h) : c->a / (c->h * c->h), -c->fixF);
   f.V = (const typename T::VR*)c->V;
   f.in = (const typename T::C*)in;
   return f;
 }
 
 template <class T>
-cudaError_t dispatch_stage(const nlse_ctx* c, const StageArgs<T>& A, cudaStream_t st) {
-  const int v = c->variant, t = c->tile_cfg;
+cudaError_t dispatch_stage(const nlse_ctx* c, const StageArgs<T>& A, const void* tmap, cudaStream_t st) {
+  LaunchCfg L;
+  L.variant = c->variant;
+  L.tile_cfg = c->tile_cfg;
+  L.tmap = tmap;
+  L.spin_limit = c->spin_limit;
+  L.extra_tx = c->extra_tx;
   switch (c->d * 10 + c->order) {
-    case 12: return launch_stage<T, 1, 2>(A, v, t, st);
-    case 14: return launch_stage<T, 1, 4>(A, v, t, st);
-    case 22: return launch_stage<T, 2, 2>(A, v, t, st);
-    case 24: return launch_stage<T, 2, 4>(A, v, t, st);
-    case 32: return launch_stage<T, 3, 2>(A, v, t, st);
-    default: return launch_stage<T, 3, 4>(A, v, t, st);
+    case 12: return launch_stage<T, 1, 2>(A, L, st);
+    case 14: return launch_stage<T, 1, 4>(A, L, st);
+    case 22: return launch_stage<T, 2, 2>(A, L, st);
+    case 24: return launch_stage<T, 2, 4>(A, L, st);
+    case 32: return launch_stage<T, 3, 2>(A, L, st);
+    default: return launch_stage<T, 3, 4>(A, L, st);
   }
+}
+
+// The TMA descriptor of stage-input buffer `buf` (0 = Psi or its FP32 copy,
+// 1 = Psi_tmp, 2 = Psi_out) for the 3D tiled kernel's tile, or nullptr when
+// the layout is not eligible (TMA needs 16-byte row pitches).
+const CUtensorMap* stage_tmap(const nlse_ctx* cc, int buf, const void* ptr) {
+  nlse_ctx* c = const_cast<nlse_ctx*>(cc);
+  if (c->d != 3 || (c->variant != 1 && c->variant != 2)) return nullptr;
+  const int tc = (c->tile_cfg < 0) ? 0 : c->tile_cfg;
+  signed char& st = c->tmap_state[tc][buf];
+  if (st == 0) {
+    st = -1;
+    int tx, ty;
+    tma_tile_shape(tc, &tx, &ty);
+    const size_t es = (c->dtype == NLSE_C128) ? 8 : 4;   // bytes of one real component
+    const cuuint64_t nx = c->n[2], ny = c->n[1], nz = c->n[0];
+    EncodeTiledFn fn = encode_fn();
+    if (fn && (2 * nx * es) % 16 == 0 && ((uintptr_t)ptr % 16) == 0) {
+      cuuint64_t dims[3] = {2 * nx, ny, nz};
+      cuuint64_t strides[2] = {2 * nx * es, 2 * nx * ny * es};
+      cuuint32_t box[3] = {cuuint32_t(2 * (tx + 4)), cuuint32_t(ty + 4), 1};
+      cuuint32_t estr[3] = {1, 1, 1};
+      CUresult r = fn(&c->tmaps[tc][buf], es == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
+                      const_cast<void*>(ptr), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                      CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+      if (r == CUDA_SUCCESS) st = 1;
+    }
+  }
+  return st == 1 ? &c->tmaps[tc][buf] : nullptr;
 }
 
 // One RK4 step = four fused stages (Eq. RK4_GPU): Psi -> Psi_tmp -> Psi_out -> Psi_tmp -> Psi.
@@ -137,6 +202,7 @@ cudaError_t launch_step(const nlse_ctx* c, double dt, cudaStream_t st) {
   C* pout = (C*)c->at(c->lay.pout);
   const C* psin = mix ? (const C*)c->at(c->lay.pn32) : (const C*)c->psi;
   const void* in[4] = {psin, ptmp, pout, ptmp};
+  const int inbuf[4] = {0, 1, 2, 1};
   C* outs[4] = {ptmp, pout, ptmp, nullptr};
   const double dtc[4] = {dt / 2.0, dt / 2.0, dt, dt / 6.0};
   for (int s = 0; s < 4; ++s) {
@@ -152,7 +218,7 @@ cudaError_t launch_step(const nlse_ctx* c, double dt, cudaStream_t st) {
     A.dt6 = dt / 6.0;
     A.stage = s + 1;
     A.flag = c->flag();
-    cudaError_t e = dispatch_stage<T>(c, A, st);
+    cudaError_t e = dispatch_stage<T>(c, A, stage_tmap(c, inbuf[s], in[s]), st);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
@@ -172,7 +238,7 @@ void drop_graph(nlse_ctx* c) {
 }
 
 int ensure_graph(nlse_ctx* c, double dt) {
-  if (c->exec && c->graph_dt == dt && c->graph_variant == c->variant) return NLSE_OK;
+  if (c->exec && c->graph_dt == dt) return NLSE_OK;
   drop_graph(c);
   if (!c->cap) {
     cudaError_t e = cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking);
@@ -206,6 +272,15 @@ int read_status(nlse_ctx* c) {
   cudaError_t e = cudaMemcpyAsync(&flag, c->flag(), sizeof(flag), cudaMemcpyDeviceToHost, c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) return cuda_fail(e, "status read");
+  if (flag & kFlagTimeoutBit) {
+    // Report once and clear every status bit: nothing a timed-out step wrote
+    // is valid (a non-finite value it produced included); the caller restores
+    // Psi and the context stays usable.
+    const unsigned int keep = 0;
+    cudaMemcpyAsync(c->flag(), &keep, sizeof(keep), cudaMemcpyHostToDevice, c->stream);
+    cudaStreamSynchronize(c->stream);
+    return fail(NLSE_ETIMEOUT, "a bounded device-side wait gave up (a TMA copy did not complete)");
+  }
   if (flag & 3u) return fail(NLSE_ENONFINITE, "non-finite value in Psi");
   return NLSE_OK;
 }
@@ -271,6 +346,7 @@ int nlse_create(nlse_t* out, int dims, const int64_t* N, double h, double a, dou
   c->lay = L;
   c->variant = 1;
   c->tile_cfg = -1;
+  c->spin_limit = kSpinLimit;
   c->graph_dt = -1.0;
 
   cudaError_t e = cudaMemsetAsync(c->at(L.status), 0, 256, c->stream);
@@ -281,6 +357,22 @@ int nlse_create(nlse_t* out, int dims, const int64_t* N, double h, double a, dou
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     memcpy(&c->vmax, &bits, sizeof(double));
   }
+  // Exact-sum stencil scale: operands must satisfy |v| < 2^(54 - F); take the
+  // largest component of Psi0 with 8x headroom for growth.
+  c->fixF = 50;
+  if (e == cudaSuccess && dtype == NLSE_C128) {
+    e = launch_vmax(psi, true, 2 * total, c->vbits(), c->stream);
+    unsigned long long bits = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&bits, c->vbits(), sizeof(bits), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    double pmax = 0.0;
+    memcpy(&pmax, &bits, sizeof(double));
+    if (pmax > 0.0 && isfinite(pmax)) {
+      int ex = 0;
+      frexp(pmax, &ex);              // pmax < 2^ex
+      c->fixF = 54 - (ex + 3);
+    }
+  }
   if (e != cudaSuccess) {
     delete c;
     return cuda_fail(e, "nlse_create");
@@ -289,10 +381,12 @@ int nlse_create(nlse_t* out, int dims, const int64_t* N, double h, double a, dou
   return NLSE_OK;
 }
 
-int nlse_set_kernel(nlse_t c, int variant) {
+int nlse_set_kernel(nlse_t c, int variant, int tile_cfg) {
   if (!c) return fail(NLSE_EINVAL, "NULL context");
-  if (variant < 0 || variant > 1) return fail(NLSE_EINVAL, "variant must be 0 or 1");
+  if (variant < 0 || variant > 3) return fail(NLSE_EINVAL, "variant must be 0..3");
+  if (tile_cfg < -1 || tile_cfg > 3) return fail(NLSE_EINVAL, "tile_cfg must be -1..3");
   c->variant = variant;
+  c->tile_cfg = tile_cfg;
   drop_graph(c);
   return NLSE_OK;
 }
@@ -335,7 +429,7 @@ int nlse_rhs(nlse_t c, const void* psi_in, void* F_out) {
     A.out = (typename T::C*)F_out;
     A.stage = 0;
     A.flag = c->flag();
-    return dispatch_stage<T>(c, A, c->stream);
+    return dispatch_stage<T>(c, A, nullptr, c->stream);
   };
   if (c->dtype == NLSE_C128) e = run(P64{});
   else if (c->dtype == NLSE_C64) e = run(P32{});
@@ -382,6 +476,24 @@ int nlse_energy(nlse_t c, double* out_host) {
   int rc = read_status(c);
   if (rc != NLSE_OK) return rc;
   *out_host = v;
+  return NLSE_OK;
+}
+
+int nlse_debug_set(nlse_t c, int key, long long value) {
+  if (!c) return fail(NLSE_EINVAL, "NULL context");
+  switch (key) {
+    case NLSE_DEBUG_SPIN_LIMIT:
+      if (value <= 0) return fail(NLSE_EINVAL, "spin limit must be > 0");
+      c->spin_limit = value;
+      break;
+    case NLSE_DEBUG_EXTRA_TX:
+      if (value < 0 || value > (1 << 20) || value % 16) return fail(NLSE_EINVAL, "extra_tx must be 0..2^20, multiple of 16");
+      c->extra_tx = (unsigned int)value;
+      break;
+    default:
+      return fail(NLSE_EINVAL, "unknown debug key");
+  }
+  drop_graph(c);
   return NLSE_OK;
 }
 

@@ -56,6 +56,10 @@ __device__ __forceinline__ R ldv(const VR* __restrict__ V, int64_t i) {
   return V ? R(__ldg(V + i)) : R(0);
 }
 
+// |z|^2 with one fixed rounding order, so every kernel computes it alike.
+template <class C2>
+__device__ __forceinline__ auto norm2(const C2 z) -> decltype(z.x) { return fma(z.x, z.x, z.y * z.y); }
+
 // The grid, the physics and the field a Laplacian is taken of.
 template <class T>
 struct Field {
@@ -69,6 +73,8 @@ struct Field {
   R cL;              // a / (12 h^2) for order 4, a / h^2 for order 2
   R tiny;            // MSD guard on |Psi_{b-1}|^2
   int bc;
+  int F;             // exact-sum stencil: fixed-point fraction bits
+  double cLF;        // exact-sum stencil: cL * 2^-F
   const typename T::VR* V;
   const typename T::C* in;   // the field (stage input Psi)
 };
@@ -96,6 +102,9 @@ struct GAcc {
     for (int k = 0; k < D; ++k) q += o[k] * f.st[k];
     return ld2<R>(f.in, q);
   }
+  // fixed-point operands of the exact-sum stencil (FP64 fields only)
+  __device__ __forceinline__ longlong2 fx0() const;
+  __device__ __forceinline__ longlong2 fx1(int k, int s) const;
 };
 
 // h^2 D_b at the face boundary site nb = c + dir e_k (Eqs. BCDlap, BCMSDlap),
@@ -108,16 +117,16 @@ __device__ __forceinline__ typename V2<typename T::R>::t ghost(const Field<T>& f
   using R = typename T::R;
   using C2 = typename V2<R>::t;
   const C2 pb = acc.at1(k, dir);
-  const R Nb = f.s * (pb.x * pb.x + pb.y * pb.y) - ldv<R>(f.V, c + dir * f.st[k]);
+  const R Nb = fma(f.s, norm2(pb), -ldv<R>(f.V, c + dir * f.st[k]));
   R fac;
   if (f.bc == BC_DIRICHLET) {
     fac = -f.h2_over_a * Nb;
   } else {
-    const R m2 = pc.x * pc.x + pc.y * pc.y;
-    const R ratio = (m2 > f.tiny) ? (dh_c.x * pc.x + dh_c.y * pc.y) / m2 : R(0);
-    fac = ratio + f.h2_over_a * (Nc - Nb);
+    const R m2 = norm2(pc);
+    const R ratio = (m2 > f.tiny) ? fma(dh_c.x, pc.x, dh_c.y * pc.y) / m2 : R(0);
+    fac = fma(f.h2_over_a, Nc - Nb, ratio);
   }
-  C2 g = {fac * pb.x - pc.x + R(2 * D) * pb.x, fac * pb.y - pc.y + R(2 * D) * pb.y};
+  C2 g = {fma(R(2 * D), pb.x, fma(fac, pb.x, -pc.x)), fma(R(2 * D), pb.y, fma(fac, pb.y, -pc.y))};
 #pragma unroll
   for (int j = 0; j < D; ++j) {
     if (j == k) continue;
@@ -129,11 +138,12 @@ __device__ __forceinline__ typename V2<typename T::R>::t ghost(const Field<T>& f
   return g;
 }
 
-// a * Lap(Psi) at interior site c with multi-index idx.
-template <class T, int D, int ORDER, class Acc>
-__device__ __forceinline__ typename V2<typename T::R>::t a_lap(const Field<T>& f, const Acc& acc, const int* idx,
-                                                               int64_t c, typename V2<typename T::R>::t pc,
-                                                               typename T::R Nc) {
+// a * Lap(Psi) at interior site c with multi-index idx; `wall` says whether
+// some +-2 neighbour lies beyond a wall (then the ghosts are used).
+template <class T, int D, int ORDER, class Acc, bool WALL>
+__device__ __forceinline__ typename V2<typename T::R>::t a_lap_body(const Field<T>& f, const Acc& acc, const int* idx,
+                                                                    int64_t c, typename V2<typename T::R>::t pc,
+                                                                    typename T::R Nc) {
   using R = typename T::R;
   using C2 = typename V2<R>::t;
   C2 s1 = {R(0), R(0)};
@@ -144,19 +154,192 @@ __device__ __forceinline__ typename V2<typename T::R>::t a_lap(const Field<T>& f
     s1.x += u.x + w.x;
     s1.y += u.y + w.y;
   }
+  const C2 dh = {fma(R(-2 * D), pc.x, s1.x), fma(R(-2 * D), pc.y, s1.y)};   // h^2 D_c
   if constexpr (ORDER == 2) {
-    return {f.cL * (s1.x - R(2 * D) * pc.x), f.cL * (s1.y - R(2 * D) * pc.y)};
+    return {f.cL * dh.x, f.cL * dh.y};
   }
-  const C2 dh = {s1.x - R(2 * D) * pc.x, s1.y - R(2 * D) * pc.y};   // h^2 D_c
   C2 s2 = {R(0), R(0)};
 #pragma unroll
   for (int k = 0; k < D; ++k) {
-    const C2 lo = (idx[k] >= 2) ? acc.at1(k, -2) : ghost<T, D>(f, acc, k, -1, c, pc, dh, Nc);
-    const C2 hi = (idx[k] <= f.n[k] - 3) ? acc.at1(k, 2) : ghost<T, D>(f, acc, k, 1, c, pc, dh, Nc);
+    C2 lo, hi;
+    if (!WALL || idx[k] >= 2) lo = acc.at1(k, -2);
+    else lo = ghost<T, D>(f, acc, k, -1, c, pc, dh, Nc);
+    if (!WALL || idx[k] <= f.n[k] - 3) hi = acc.at1(k, 2);
+    else hi = ghost<T, D>(f, acc, k, 1, c, pc, dh, Nc);
     s2.x += lo.x + hi.x;
     s2.y += lo.y + hi.y;
   }
-  return {f.cL * (R(16) * s1.x - s2.x - R(30 * D) * pc.x), f.cL * (R(16) * s1.y - s2.y - R(30 * D) * pc.y)};
+  return {f.cL * fma(R(-30 * D), pc.x, fma(R(16), s1.x, -s2.x)), f.cL * fma(R(-30 * D), pc.y, fma(R(16), s1.y, -s2.y))};
+}
+
+template <class T, int D, int ORDER, class Acc>
+__device__ __forceinline__ typename V2<typename T::R>::t a_lap_wall(const Field<T>& f, const Acc& acc, const int* idx,
+                                                                 int64_t c, typename V2<typename T::R>::t pc,
+                                                                 typename T::R Nc) {
+  return a_lap_body<T, D, ORDER, Acc, true>(f, acc, idx, c, pc, Nc);
+}
+
+template <int D>
+__device__ __forceinline__ bool near_wall2(const int* idx, const int* n) {
+  bool w = false;
+#pragma unroll
+  for (int k = 0; k < D; ++k) w |= (idx[k] < 2) | (idx[k] > n[k] - 3);
+  return w;
+}
+
+template <class T, int D, int ORDER, class Acc>
+__device__ __forceinline__ typename V2<typename T::R>::t a_lap(const Field<T>& f, const Acc& acc, const int* idx,
+                                                               int64_t c, typename V2<typename T::R>::t pc,
+                                                               typename T::R Nc) {
+  if (ORDER == 4 && near_wall2<D>(idx, f.n)) return a_lap_wall<T, D, ORDER>(f, acc, idx, c, pc, Nc);
+  return a_lap_body<T, D, ORDER, Acc, false>(f, acc, idx, c, pc, Nc);
+}
+
+// ---------------------------------------------------------------------------
+// Exact-sum stencil for the FP64 path.  GB300 issues FP64 arithmetic at
+// 1/75 of the FP32 rate, so the FP64 stage is bound by the FP64 pipe, and
+// most of its FP64 instructions are the stencil's additions.  Here every
+// stencil operand is converted (on the integer pipe, from its IEEE-754 bits)
+// to a 64-bit fixed-point number v * 2^F rounded to nearest; the sums
+// 16 s1 - s2 - 30 d Psi_c (or s1 - 2d Psi_c) are then exact integers, and one
+// conversion and one multiply by cL 2^-F give a*Lap in FP64.  F is chosen per
+// context so that |v| < 2^(54-F) covers the state with headroom; an operand
+// outside that range (or Inf/NaN) yields kFixBad and the site falls back to
+// the FP64 stencil, so the result is always defined.
+// ---------------------------------------------------------------------------
+constexpr long long kFixBad = (long long)0x8000000000000000ull;
+
+__device__ __forceinline__ long long fix1(double v, int F) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(v);
+  const int e = int((u >> 52) & 0x7FF);
+  const long long m = (long long)((u & 0x000FFFFFFFFFFFFFull) | 0x0010000000000000ull);
+  const int sh = e - 1075 + F;
+  long long r;
+  if (e == 0) return 0;                 // zero or subnormal: below any usable resolution
+  if (sh > 1) return kFixBad;           // out of range, or Inf / NaN (e = 2047)
+  if (sh >= 0) r = m << sh;
+  else if (sh >= -54) { const int k = -sh; r = (m + (1ll << (k - 1))) >> k; }
+  else r = 0;
+  return (u >> 63) ? -r : r;
+}
+__device__ __forceinline__ longlong2 fix2(double2 v, int F) { return make_longlong2(fix1(v.x, F), fix1(v.y, F)); }
+__device__ __forceinline__ bool fbad(longlong2 v) { return (v.x == kFixBad) | (v.y == kFixBad); }
+
+// The FP64 stencil as an out-of-line call (out-of-range operands).
+template <class T, int D, int ORDER, class Acc>
+__device__ __forceinline__ double2 a_lap_slow(const Field<T>& f, const Acc& acc, const int* idx, int64_t c, double2 pc,
+                                           double Nc) {
+  return a_lap_body<T, D, ORDER, Acc, true>(f, acc, idx, c, pc, Nc);
+}
+
+// s2 = sum over axes of Psi_{+2} + Psi_{-2} in fixed point at a site next to a
+// wall, with the ghosts (computed in FP64 like the FP64 stencil) in place of
+// the values beyond the wall.  Out of line: only wall-adjacent sites call it.
+template <class T, int D, class Acc>
+__device__ __forceinline__ longlong2 exact_s2_wall(const Field<T>& f, const Acc& acc, const int* idx, int64_t c,
+                                                double2 pc, double Nc, bool* bad) {
+  double2 t = {0.0, 0.0};
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    const double2 u = acc.at1(k, 1), w = acc.at1(k, -1);
+    t.x += u.x + w.x;
+    t.y += u.y + w.y;
+  }
+  const double2 dh = {fma(double(-2 * D), pc.x, t.x), fma(double(-2 * D), pc.y, t.y)};   // h^2 D_c in FP64
+  long long sx = 0, sy = 0;
+  bool b = false;
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    longlong2 lo, hi;
+    if (idx[k] >= 2) lo = acc.fx1(k, -2);
+    else lo = fix2(ghost<T, D>(f, acc, k, -1, c, pc, dh, Nc), f.F);
+    if (idx[k] <= f.n[k] - 3) hi = acc.fx1(k, 2);
+    else hi = fix2(ghost<T, D>(f, acc, k, 1, c, pc, dh, Nc), f.F);
+    b |= fbad(lo) | fbad(hi);
+    sx += lo.x + hi.x;
+    sy += lo.y + hi.y;
+  }
+  *bad |= b;
+  return make_longlong2(sx, sy);
+}
+
+template <class T, int D, int ORDER, class Acc>
+__device__ __forceinline__ double2 a_lap_exact(const Field<T>& f, const Acc& acc, const int* idx, int64_t c,
+                                               double2 pc, double Nc) {
+  static_assert(std::is_same<typename T::R, double>::value, "exact-sum stencil is FP64 only");
+  const longlong2 cc = acc.fx0();
+  bool bad = fbad(cc);
+  long long s1x = 0, s1y = 0;
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    const longlong2 u = acc.fx1(k, 1), w = acc.fx1(k, -1);
+    bad |= fbad(u) | fbad(w);
+    s1x += u.x + w.x;
+    s1y += u.y + w.y;
+  }
+  if constexpr (ORDER == 2) {
+    if (bad) return a_lap_slow<T, D, ORDER>(f, acc, idx, c, pc, Nc);
+    return {f.cLF * __ll2double_rn(s1x - 2 * D * cc.x), f.cLF * __ll2double_rn(s1y - 2 * D * cc.y)};
+  }
+  const bool wall = near_wall2<D>(idx, f.n);
+  long long s2x = 0, s2y = 0;
+  if (!wall) {
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      const longlong2 lo = acc.fx1(k, -2), hi = acc.fx1(k, 2);
+      bad |= fbad(lo) | fbad(hi);
+      s2x += lo.x + hi.x;
+      s2y += lo.y + hi.y;
+    }
+  } else {
+    const longlong2 s2 = exact_s2_wall<T, D>(f, acc, idx, c, pc, Nc, &bad);
+    s2x = s2.x;
+    s2y = s2.y;
+  }
+  if (bad) return a_lap_slow<T, D, ORDER>(f, acc, idx, c, pc, Nc);
+  const long long Sx = 16 * s1x - s2x - 30 * D * cc.x;
+  const long long Sy = 16 * s1y - s2y - 30 * D * cc.y;
+  return {f.cLF * __ll2double_rn(Sx), f.cLF * __ll2double_rn(Sy)};
+}
+
+// The exact-sum Laplacian at a deep-interior site (no wall within two cells):
+// the same integer sums as a_lap_exact without its wall branch.
+template <class T, int D, int ORDER, class Acc>
+__device__ __forceinline__ double2 a_lap_exact_deep(const Field<T>& f, const Acc& acc, const int* idx, int64_t c,
+                                                    double2 pc, double Nc) {
+  const longlong2 cc = acc.fx0();
+  bool bad = fbad(cc);
+  long long s1x = 0, s1y = 0;
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    const longlong2 u = acc.fx1(k, 1), w = acc.fx1(k, -1);
+    bad |= fbad(u) | fbad(w);
+    s1x += u.x + w.x;
+    s1y += u.y + w.y;
+  }
+  if constexpr (ORDER == 2) {
+    if (bad) return a_lap_slow<T, D, ORDER>(f, acc, idx, c, pc, Nc);
+    return {f.cLF * __ll2double_rn(s1x - 2 * D * cc.x), f.cLF * __ll2double_rn(s1y - 2 * D * cc.y)};
+  }
+  long long s2x = 0, s2y = 0;
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    const longlong2 lo = acc.fx1(k, -2), hi = acc.fx1(k, 2);
+    bad |= fbad(lo) | fbad(hi);
+    s2x += lo.x + hi.x;
+    s2y += lo.y + hi.y;
+  }
+  if (bad) return a_lap_slow<T, D, ORDER>(f, acc, idx, c, pc, Nc);
+  const long long Sx = 16 * s1x - s2x - 30 * D * cc.x;
+  const long long Sy = 16 * s1y - s2y - 30 * D * cc.y;
+  return {f.cLF * __ll2double_rn(Sx), f.cLF * __ll2double_rn(Sy)};
+}
+
+template <class T, int D>
+__device__ __forceinline__ longlong2 GAcc<T, D>::fx0() const { return fix2(ld2<double>(f.in, c), f.F); }
+template <class T, int D>
+__device__ __forceinline__ longlong2 GAcc<T, D>::fx1(int k, int s) const {
+  return fix2(ld2<double>(f.in, c + s * f.st[k]), f.F);
 }
 
 // Everything a stage writes, on top of the field it reads.
@@ -174,38 +357,54 @@ struct StageArgs {
   unsigned int* flag;          // bit 0: non-finite Psi
 };
 
+// The pointwise operands of one site's update, loaded ahead of use.
 template <class T>
-__device__ __forceinline__ void rk_update(const StageArgs<T>& A, int64_t i, typename V2<typename T::R>::t F) {
+struct PointVals {
+  typename T::R v;      // V at the site
+  typename T::C pn;     // Psi^n (stage precision), stages 1-3
+  typename T::C K;      // K_tot, stages 2-4
+  typename T::M mst;    // master Psi^n, stage 4
+};
+
+// S = the stage when known at compile time, -1 = read A.stage.
+template <class T, int S = -1>
+__device__ __forceinline__ PointVals<T> load_point(const StageArgs<T>& A, int64_t i, bool with_v) {
+  PointVals<T> p;
+  const int st = (S >= 0) ? S : A.stage;
+  p.v = with_v ? ldv<typename T::R>(A.f.V, i) : typename T::R(0);
+  if (st >= 1 && st <= 3) p.pn = A.psin[i];
+  if (st >= 2) p.K = A.ktot[i];
+  if (st == 4) p.mst = A.master[i];
+  return p;
+}
+
+// Apply stage A.stage of Eq. RK4_GPU at site i with k = F.
+template <class T, int S = -1>
+__device__ __forceinline__ void rk_apply(const StageArgs<T>& A, int64_t i, typename V2<typename T::R>::t F,
+                                         const PointVals<T>& p) {
   using R = typename T::R;
   using C = typename T::C;
-  switch (A.stage) {
+  switch ((S >= 0) ? S : A.stage) {
     case 0:
       A.out[i] = C{F.x, F.y};
       break;
-    case 1: {  // K_tot = k; Psi_tmp = Psi^n + (dt/2) k
+    case 1:  // K_tot = k; Psi_tmp = Psi^n + (dt/2) k
       A.ktot[i] = C{F.x, F.y};
-      const C p = A.psin[i];
-      A.out[i] = C{fma(A.dtc, F.x, p.x), fma(A.dtc, F.y, p.y)};
+      A.out[i] = C{fma(A.dtc, F.x, p.pn.x), fma(A.dtc, F.y, p.pn.y)};
       break;
-    }
     case 2:
-    case 3: {  // K_tot += 2k; Psi_out = Psi^n + (dt/2) k  |  Psi_tmp = Psi^n + dt k
-      const C K = A.ktot[i];
-      A.ktot[i] = C{fma(R(2), F.x, K.x), fma(R(2), F.y, K.y)};
-      const C p = A.psin[i];
-      A.out[i] = C{fma(A.dtc, F.x, p.x), fma(A.dtc, F.y, p.y)};
+    case 3:  // K_tot += 2k; Psi_out = Psi^n + (dt/2) k  |  Psi_tmp = Psi^n + dt k
+      A.ktot[i] = C{fma(R(2), F.x, p.K.x), fma(R(2), F.y, p.K.y)};
+      A.out[i] = C{fma(A.dtc, F.x, p.pn.x), fma(A.dtc, F.y, p.pn.y)};
       break;
-    }
     default: {  // Psi^{n+1} = Psi^n + (dt/6)(K_tot + k)
-      const C K = A.ktot[i];
-      const typename T::M p = A.master[i];
       typename T::M q;
       if constexpr (std::is_same<typename T::M, C>::value) {
-        q.x = fma(A.dtc, K.x + F.x, p.x);
-        q.y = fma(A.dtc, K.y + F.y, p.y);
+        q.x = fma(A.dtc, p.K.x + F.x, p.mst.x);
+        q.y = fma(A.dtc, p.K.y + F.y, p.mst.y);
       } else {  // FP64 accumulator over FP32 stages
-        q.x = fma(A.dt6, double(K.x) + double(F.x), double(p.x));
-        q.y = fma(A.dt6, double(K.y) + double(F.y), double(p.y));
+        q.x = fma(A.dt6, double(p.K.x) + double(F.x), double(p.mst.x));
+        q.y = fma(A.dt6, double(p.K.y) + double(F.y), double(p.mst.y));
         A.n32[i] = C{R(q.x), R(q.y)};
       }
       A.master[i] = q;
@@ -215,49 +414,42 @@ __device__ __forceinline__ void rk_update(const StageArgs<T>& A, int64_t i, type
   }
 }
 
-// The full per-site work: F at interior site c, its update, and the update of
-// every boundary site whose b-1 neighbour is c.
-template <class T, int D, int ORDER, class Acc>
-__device__ __forceinline__ void process_site(const StageArgs<T>& A, const Acc& acc, const int* idx, int64_t c) {
+template <class T>
+__device__ __forceinline__ void rk_update(const StageArgs<T>& A, int64_t i, typename V2<typename T::R>::t F) {
+  rk_apply<T>(A, i, F, load_point<T>(A, i, false));
+}
+
+// Update every boundary site whose b-1 neighbour is the interior site c
+// (c + sum_k o_k e_k with o_k in {0} u {-1 if idx==1} u {+1 if idx==n-2}, not
+// all 0), with F_b = 0 (Dirichlet) or F_b = i Im(F_c / Psi_c) Psi_b (MSD).
+// Out of line: only sites next to a wall call it.
+template <class T, int D, class Acc>
+__device__ __forceinline__ void serve_walls(const StageArgs<T>& A, const Acc& acc, const int* idx, int64_t c,
+                                         typename V2<typename T::R>::t pc, typename V2<typename T::R>::t F) {
   using R = typename T::R;
   using C2 = typename V2<R>::t;
   const Field<T>& f = A.f;
-  const C2 pc = acc.at0();
-  const R Nc = f.s * (pc.x * pc.x + pc.y * pc.y) - ldv<R>(f.V, c);
-  const C2 aL = a_lap<T, D, ORDER>(f, acc, idx, c, pc, Nc);
-  const C2 F = {-(aL.y + Nc * pc.y), aL.x + Nc * pc.x};
-  rk_update<T>(A, c, F);
-
-  bool near = false;
-#pragma unroll
-  for (int k = 0; k < D; ++k) near |= (idx[k] == 1) | (idx[k] == f.n[k] - 2);
-  if (!near) return;
   R theta = R(0);
   if (f.bc == BC_MSD) {
-    const R m2 = pc.x * pc.x + pc.y * pc.y;
-    if (m2 > f.tiny) theta = (F.y * pc.x - F.x * pc.y) / m2;
+    const R m2 = norm2(pc);
+    if (m2 > f.tiny) theta = fma(F.y, pc.x, -(F.x * pc.y)) / m2;
   }
-  // boundary sites c + sum_k o_k e_k with o_k in {0} u {-1 if idx==1} u {+1 if idx==n-2}, not all 0
-  int opts[D][3], nopt[D];
-  int combos = 1;
+  // all offsets o in {-1, 0, 1}^D except 0, where -1 needs idx == 1 and +1 needs idx == n - 2
 #pragma unroll
-  for (int k = 0; k < D; ++k) {
-    nopt[k] = 0;
-    opts[k][nopt[k]++] = 0;
-    if (idx[k] == 1) opts[k][nopt[k]++] = -1;
-    if (idx[k] == f.n[k] - 2) opts[k][nopt[k]++] = 1;
-    combos *= nopt[k];
-  }
-  for (int q = 1; q < combos; ++q) {
-    int r = q;
+  for (int q = 1; q < (D == 1 ? 3 : (D == 2 ? 9 : 27)); ++q) {
     int o[D];
+    int r = q;
+    bool ok = true;
     int64_t b = c;
 #pragma unroll
     for (int k = D - 1; k >= 0; --k) {
-      o[k] = opts[k][r % nopt[k]];
+      const int v = r % 3;
+      r /= 3;
+      o[k] = (v == 2) ? -1 : v;
+      ok &= (o[k] == 0) | ((o[k] == -1) & (idx[k] == 1)) | ((o[k] == 1) & (idx[k] == f.n[k] - 2));
       b += o[k] * f.st[k];
-      r /= nopt[k];
     }
+    if (!ok) continue;
     C2 Fb = {R(0), R(0)};
     if (f.bc == BC_MSD) {
       const C2 pb = acc.atv(o);
@@ -267,8 +459,46 @@ __device__ __forceinline__ void process_site(const StageArgs<T>& A, const Acc& a
   }
 }
 
+// The full per-site work: F at interior site c, its update, and the update of
+// every boundary site whose b-1 neighbour is c.  `p` holds c's pointwise
+// operands (load_point).
+template <class T, int D, int ORDER, bool EXACT, class Acc>
+__device__ __forceinline__ void process_site_pv(const StageArgs<T>& A, const Acc& acc, const int* idx, int64_t c,
+                                                const PointVals<T>& p) {
+  using R = typename T::R;
+  using C2 = typename V2<R>::t;
+  const Field<T>& f = A.f;
+  const C2 pc = acc.at0();
+  const R Nc = fma(f.s, norm2(pc), -p.v);
+  C2 aL;
+  if constexpr (EXACT) aL = a_lap_exact<T, D, ORDER>(f, acc, idx, c, pc, Nc);
+  else aL = a_lap<T, D, ORDER>(f, acc, idx, c, pc, Nc);
+  const C2 F = {-fma(Nc, pc.y, aL.y), fma(Nc, pc.x, aL.x)};
+  rk_apply<T>(A, c, F, p);
+
+  bool near = false;
+#pragma unroll
+  for (int k = 0; k < D; ++k) near |= (idx[k] == 1) | (idx[k] == f.n[k] - 2);
+  if (near) serve_walls<T, D>(A, acc, idx, c, pc, F);
+}
+
+template <class T, int D, int ORDER, bool EXACT, class Acc>
+__device__ __forceinline__ void process_site(const StageArgs<T>& A, const Acc& acc, const int* idx, int64_t c) {
+  process_site_pv<T, D, ORDER, EXACT>(A, acc, idx, c, load_point<T>(A, c, true));
+}
+
+// How a stage is launched: kernel variant, CTA tile, and (3D tiled kernel)
+// the TMA descriptor of the stage input when the layout allows TMA.
+struct LaunchCfg {
+  int variant;
+  int tile_cfg;
+  const void* tmap;        // CUtensorMap* of A.f.in for the tile's box, or nullptr
+  long long spin_limit;    // bound on any device-side wait, in SM clock cycles
+  unsigned int extra_tx;   // test hook: extra bytes every TMA barrier waits for (0 in normal use)
+};
+
 // Host-visible launch entry points (defined in stage_*.cu).
 template <class T, int D, int ORDER>
-cudaError_t launch_stage(const StageArgs<T>& A, int variant, int tile_cfg, cudaStream_t stream);
+cudaError_t launch_stage(const StageArgs<T>& A, const LaunchCfg& L, cudaStream_t stream);
 
 }  // namespace nlse

@@ -9,6 +9,16 @@ namespace nlse {
 
 constexpr int kMaxReduceBlocks = 1024;
 
+// CTA tile (x-by-y threads) of the tiled 3D/2D kernels for tile_cfg 0..3.
+inline void tma_tile_shape(int tile_cfg, int* tx, int* ty) {
+  switch (tile_cfg) {
+    case 1: *tx = 64; *ty = 4; break;
+    case 2: *tx = 32; *ty = 16; break;
+    case 3: *tx = 64; *ty = 8; break;
+    default: *tx = 32; *ty = 8; break;
+  }
+}
+
 cudaError_t launch_mass(const void* psi, bool psi_double, int64_t total, double scale, double* partials,
                         double* result, unsigned int* flag, cudaStream_t stream);
 template <class T, int D, int ORDER>

@@ -55,7 +55,7 @@ __global__ void __launch_bounds__(256) k_mass(const C* __restrict__ psi, int64_t
   bool bad = false;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
     const double2 p = ld2<double>(psi, i);
-    const double m2 = p.x * p.x + p.y * p.y;
+    const double m2 = norm2(p);
     bad |= !isfinite(m2);
     nadd(acc, m2);
   }
@@ -80,12 +80,12 @@ __global__ void __launch_bounds__(256) k_energy(const Field<T> f, double* partia
       c += idx[k] * f.st[k];
     }
     const double2 pc = ld2<double>(f.in, c);
-    const double m2 = pc.x * pc.x + pc.y * pc.y;
+    const double m2 = norm2(pc);
     const double v = ldv<double>(f.V, c);
-    const double Nc = f.s * m2 - v;
+    const double Nc = fma(f.s, m2, -v);
     const GAcc<T, D> ga(f, c);
     const double2 aL = a_lap<T, D, ORDER>(f, ga, idx, c, pc, Nc);
-    const double e = -(pc.x * aL.x + pc.y * aL.y) + v * m2 - 0.5 * f.s * m2 * m2;
+    const double e = fma(-0.5 * f.s, m2 * m2, fma(v, m2, -fma(pc.x, aL.x, pc.y * aL.y)));
     bad |= !isfinite(e);
     nadd(acc, e);
   }

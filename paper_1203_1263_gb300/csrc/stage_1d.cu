@@ -4,12 +4,16 @@
 namespace nlse {
 
 template <class T, int D, int ORDER>
-cudaError_t launch_stage(const StageArgs<T>& A, int variant, int tile_cfg, cudaStream_t stream) {
-  (void)variant; (void)tile_cfg;
+cudaError_t launch_stage(const StageArgs<T>& A, const LaunchCfg& L, cudaStream_t stream) {
+  const int variant = L.variant, tile_cfg = L.tile_cfg;
+  (void)tile_cfg;
+  if constexpr (std::is_same<typename T::R, double>::value) {
+    if (variant >= 2) return launch_generic<T, D, ORDER, true>(A, stream);
+  }
   return launch_generic<T, D, ORDER>(A, stream);
 }
 
-#define INST(T, O) template cudaError_t launch_stage<T, 1, O>(const StageArgs<T>&, int, int, cudaStream_t);
+#define INST(T, O) template cudaError_t launch_stage<T, 1, O>(const StageArgs<T>&, const LaunchCfg&, cudaStream_t);
 INST(P64, 2) INST(P64, 4) INST(P32, 2) INST(P32, 4) INST(PMix, 2) INST(PMix, 4)
 #undef INST
 

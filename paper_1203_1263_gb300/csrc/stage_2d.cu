@@ -1,15 +1,35 @@
-// 2D stage launches (generic kernel; tiled kernel in variant 1).
+// 2D stage launches: variant 0 = generic kernel, 1 = halo-tiled kernel,
+// 2 / 3 = tiled / generic with the exact-sum stencil (FP64 only).
 #include "stage_generic.cuh"
+#include "stage_tiled.cuh"
 
 namespace nlse {
 
 template <class T, int D, int ORDER>
-cudaError_t launch_stage(const StageArgs<T>& A, int variant, int tile_cfg, cudaStream_t stream) {
-  (void)variant; (void)tile_cfg;
-  return launch_generic<T, D, ORDER>(A, stream);
+cudaError_t launch_stage(const StageArgs<T>& A, const LaunchCfg& L, cudaStream_t stream) {
+  constexpr bool fp64 = std::is_same<typename T::R, double>::value;
+  const int variant = (!fp64 && L.variant >= 2) ? L.variant - 2 : L.variant;   // exact sums are FP64 only
+  const bool exact = variant >= 2;
+  if (variant == 0 || variant == 3) {
+    if constexpr (fp64) if (exact) return launch_generic<T, D, ORDER, true>(A, stream);
+    return launch_generic<T, D, ORDER>(A, stream);
+  }
+  // tiled: deep interior + the wall shell
+  cudaError_t e = cudaSuccess;
+  if (has_deep(D, A.f.m)) {
+    if constexpr (fp64) {
+      if (exact) e = launch2d_tiled<T, ORDER, true>(A, L.tile_cfg, stream);
+      else e = launch2d_tiled<T, ORDER>(A, L.tile_cfg, stream);
+    } else {
+      e = launch2d_tiled<T, ORDER>(A, L.tile_cfg, stream);
+    }
+    if (e != cudaSuccess) return e;
+  }
+  if constexpr (fp64) if (exact) return launch_shell<T, D, ORDER, true>(A, stream);
+  return launch_shell<T, D, ORDER>(A, stream);
 }
 
-#define INST(T, O) template cudaError_t launch_stage<T, 2, O>(const StageArgs<T>&, int, int, cudaStream_t);
+#define INST(T, O) template cudaError_t launch_stage<T, 2, O>(const StageArgs<T>&, const LaunchCfg&, cudaStream_t);
 INST(P64, 2) INST(P64, 4) INST(P32, 2) INST(P32, 4) INST(PMix, 2) INST(PMix, 4)
 #undef INST
 

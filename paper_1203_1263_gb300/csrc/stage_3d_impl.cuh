@@ -1,0 +1,37 @@
+// 3D stage launches: variant 0 = generic kernel, 1 = z-marching tiled kernel
+// (TMA-fed when the layout allows, else cooperative loads),
+// 2 / 3 = tiled / generic with the exact-sum stencil (FP64 only).
+// Included by one small translation unit per (precision, order), so that the
+// many kernel instantiations compile in parallel.
+#pragma once
+#include "stage_generic.cuh"
+#include "stage_tiled.cuh"
+#include "stage_tma.cuh"
+
+namespace nlse {
+
+template <class T, int D, int ORDER>
+cudaError_t launch_stage(const StageArgs<T>& A, const LaunchCfg& L, cudaStream_t stream) {
+  constexpr bool fp64 = std::is_same<typename T::R, double>::value;
+  const int variant = (!fp64 && L.variant >= 2) ? L.variant - 2 : L.variant;   // exact sums are FP64 only
+  const bool exact = variant >= 2;
+  if (variant == 0 || variant == 3) {
+    if constexpr (fp64) if (exact) return launch_generic<T, D, ORDER, true>(A, stream);
+    return launch_generic<T, D, ORDER>(A, stream);
+  }
+  // tiled: deep interior (TMA-fed when the layout allows) + the wall shell
+  cudaError_t e = cudaSuccess;
+  if (has_deep(D, A.f.m)) {
+    if constexpr (fp64) {
+      if (exact) e = L.tmap ? launch3d_tma<T, ORDER, true>(A, L, stream) : launch3d_tiled<T, ORDER, true>(A, L.tile_cfg, stream);
+      else e = L.tmap ? launch3d_tma<T, ORDER, false>(A, L, stream) : launch3d_tiled<T, ORDER>(A, L.tile_cfg, stream);
+    } else {
+      e = L.tmap ? launch3d_tma<T, ORDER, false>(A, L, stream) : launch3d_tiled<T, ORDER>(A, L.tile_cfg, stream);
+    }
+    if (e != cudaSuccess) return e;
+  }
+  if constexpr (fp64) if (exact) return launch_shell<T, D, ORDER, true>(A, stream);
+  return launch_shell<T, D, ORDER>(A, stream);
+}
+
+}  // namespace nlse

@@ -1,0 +1,6 @@
+// 3D stage launches for P32, order 4 (see stage_3d_impl.cuh).
+#include "stage_3d_impl.cuh"
+
+namespace nlse {
+template cudaError_t launch_stage<P32, 3, 4>(const StageArgs<P32>&, const LaunchCfg&, cudaStream_t);
+}  // namespace nlse

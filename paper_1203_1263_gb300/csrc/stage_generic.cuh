@@ -7,7 +7,7 @@
 
 namespace nlse {
 
-template <class T, int D, int ORDER>
+template <class T, int D, int ORDER, bool EXACT>
 __global__ void __launch_bounds__(256) k_stage_generic(const StageArgs<T> A) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= A.f.ninterior) return;
@@ -21,15 +21,113 @@ __global__ void __launch_bounds__(256) k_stage_generic(const StageArgs<T> A) {
     c += idx[k] * A.f.st[k];
   }
   const GAcc<T, D> acc(A.f, c);
-  process_site<T, D, ORDER>(A, acc, idx, c);
+  process_site<T, D, ORDER, EXACT>(A, acc, idx, c);
 }
 
-template <class T, int D, int ORDER>
+// ---------------------------------------------------------------------------
+// Wall shell: the interior sites within one cell of a wall (some index equal
+// to 1 or N-2).  The tiled kernels compute only the deep interior (every
+// index in [2, N-3]), where the stencil never reaches past a wall and no
+// boundary site is served; the shell kernel computes the rest with the
+// generic per-site code.  Sites are enumerated exactly, face by face: with
+// interior extents a_k = N_k - 2, deep extents d_k = max(a_k - 2, 0) and
+// c_k = a_k - d_k (2, or 1 when a_k == 1), the shell is
+//   {i_0 in the c_0 outer layers} x a_1 x a_2
+//   + d_0 x {i_1 in the c_1 outer layers} x a_2 + d_0 x d_1 x {c_2 outer layers}.
+// ---------------------------------------------------------------------------
+template <class T, int D>
+__device__ __forceinline__ int64_t shell_decode(const Field<T>& f, int64_t t, int* idx) {
+  int a[3], d[3], c[3];
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    a[k] = f.m[k];
+    d[k] = a[k] > 2 ? a[k] - 2 : 0;
+    c[k] = a[k] - d[k];
+  }
+  auto outer = [&](int k, int q) { return q == 0 ? 1 : f.n[k] - 2; };   // q-th outer layer of axis k
+  if constexpr (D == 1) {
+    idx[0] = outer(0, int(t));
+  } else if constexpr (D == 2) {
+    const int64_t F0 = (int64_t)c[0] * a[1];
+    if (t < F0) {
+      idx[0] = outer(0, int(t / a[1]));
+      idx[1] = 1 + int(t % a[1]);
+    } else {
+      t -= F0;
+      idx[0] = 2 + int(t / c[1]);
+      idx[1] = outer(1, int(t % c[1]));
+    }
+  } else {
+    const int64_t F0 = (int64_t)c[0] * a[1] * a[2];
+    const int64_t F1 = (int64_t)d[0] * c[1] * a[2];
+    if (t < F0) {
+      const int64_t pa = (int64_t)a[1] * a[2];
+      idx[0] = outer(0, int(t / pa));
+      const int64_t r = t % pa;
+      idx[1] = 1 + int(r / a[2]);
+      idx[2] = 1 + int(r % a[2]);
+    } else if (t < F0 + F1) {
+      t -= F0;
+      const int64_t pa = (int64_t)c[1] * a[2];
+      idx[0] = 2 + int(t / pa);
+      const int64_t r = t % pa;
+      idx[1] = outer(1, int(r / a[2]));
+      idx[2] = 1 + int(r % a[2]);
+    } else {
+      t -= F0 + F1;
+      const int64_t pa = (int64_t)d[1] * c[2];
+      idx[0] = 2 + int(t / pa);
+      const int64_t r = t % pa;
+      idx[1] = 2 + int(r / c[2]);
+      idx[2] = outer(2, int(r % c[2]));
+    }
+  }
+  int64_t s = 0;
+#pragma unroll
+  for (int k = 0; k < D; ++k) s += idx[k] * f.st[k];
+  return s;
+}
+
+inline int64_t shell_count(int D, const int* m) {
+  int64_t all = 1, deep = 1;
+  for (int k = 0; k < D; ++k) {
+    all *= m[k];
+    deep *= (m[k] > 2 ? m[k] - 2 : 0);
+  }
+  return all - deep;
+}
+
+inline bool has_deep(int D, const int* m) {
+  for (int k = 0; k < D; ++k)
+    if (m[k] <= 2) return false;
+  return true;
+}
+
+template <class T, int D, int ORDER, bool EXACT>
+__global__ void __launch_bounds__(256) k_stage_shell(const StageArgs<T> A, int64_t nshell) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nshell) return;
+  int idx[D];
+  const int64_t c = shell_decode<T, D>(A.f, t, idx);
+  const GAcc<T, D> acc(A.f, c);
+  process_site<T, D, ORDER, EXACT>(A, acc, idx, c);
+}
+
+template <class T, int D, int ORDER, bool EXACT = false>
+cudaError_t launch_shell(const StageArgs<T>& A, cudaStream_t stream) {
+  const int64_t ns = shell_count(D, A.f.m);
+  if (ns <= 0) return cudaSuccess;
+  const int threads = 256;
+  k_stage_shell<T, D, ORDER, EXACT><<<dim3((unsigned)((ns + threads - 1) / threads)), threads, 0, stream>>>(A, ns);
+  return cudaGetLastError();
+}
+
+template <class T, int D, int ORDER, bool EXACT = false>
 cudaError_t launch_generic(const StageArgs<T>& A, cudaStream_t stream) {
   if (A.f.ninterior <= 0) return cudaSuccess;
   const int threads = 256;
   const int64_t blocks = (A.f.ninterior + threads - 1) / threads;
-  k_stage_generic<T, D, ORDER><<<dim3((unsigned)blocks), threads, 0, stream>>>(A);
+  k_stage_generic<T, D, ORDER, EXACT><<<dim3((unsigned)blocks), threads, 0, stream>>>(A);
   return cudaGetLastError();
 }
 

@@ -105,8 +105,12 @@ class Integrator:
     def sync(self) -> None:
         L.check(self.lib.nlse_sync(self.ctx))
 
-    def set_kernel(self, variant: int) -> None:
-        L.check(self.lib.nlse_set_kernel(self.ctx, int(variant)))
+    def set_kernel(self, variant: int, tile_cfg: int = -1) -> None:
+        L.check(self.lib.nlse_set_kernel(self.ctx, int(variant), int(tile_cfg)))
+
+    def debug_set(self, key: int, value: int) -> None:
+        """Test hook for the bounded device-side waits (see nlse_debug_set)."""
+        L.check(self.lib.nlse_debug_set(self.ctx, int(key), int(value)))
 
     def max_dt(self, s_rho_max: float = 0.0, vmax: Optional[float] = None) -> float:
         if vmax is None:

@@ -86,7 +86,7 @@ def oracle_rk4_cached(key, *args):
 @pytest.mark.parametrize("order", [2, 4])
 @pytest.mark.parametrize("bc", ["dirichlet", "msd"])
 @pytest.mark.parametrize("dtype", ["c128", "c64", "c64_acc64"])
-@pytest.mark.parametrize("variant", [0, 1])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3])
 def test_step_matches_oracle(dims, shape, order, bc, dtype, variant):
     h, a, s = 0.35, 0.8, -1.1
     psi, V = problem(shape, 100 + dims * 10 + order)
@@ -132,7 +132,7 @@ def test_mass_energy_match_oracle(dims, shape, order, bc, dtype):
 
 
 @pytest.mark.parametrize("dtype", ["c128", "c64", "c64_acc64"])
-@pytest.mark.parametrize("variant", [0, 1])
+@pytest.mark.parametrize("variant", [0, 1, 2])
 def test_split_continuation_and_determinism_bitwise(dtype, variant):
     psi, V = problem((11, 12, 40), 3)
     h, a, s, order = 0.3, 0.6, 1.0, 4
@@ -148,8 +148,9 @@ def test_split_continuation_and_determinism_bitwise(dtype, variant):
 
 
 @pytest.mark.parametrize("dtype", ["c128", "c64", "c64_acc64"])
-@pytest.mark.parametrize("dims,shape", [(2, (19, 45)), (3, (9, 21, 70)), (3, (20, 17, 64))])
-def test_tiled_kernel_equals_generic_bitwise(dtype, dims, shape):
+@pytest.mark.parametrize("dims,shape", [(2, (19, 45)), (3, (9, 21, 70)), (3, (20, 17, 64)), (3, (5, 40, 131))])
+@pytest.mark.parametrize("tile_cfg", [0, 1, 2, 3])
+def test_tiled_kernel_equals_generic_bitwise(dtype, dims, shape, tile_cfg):
     """The tiled kernels perform the generic kernel's arithmetic in the same
     order; only where the operands come from differs."""
     for order in (2, 4):
@@ -158,12 +159,56 @@ def test_tiled_kernel_equals_generic_bitwise(dtype, dims, shape):
             h, a, s = 0.3, 0.6, -1.0
             dt = stable_dt(shape, h, a, s, order, V)
             res = []
-            for variant in (0, 1):
+            for variant in (0, 1, 3, 2):
                 g = Integrator(psi, h, a, s, V, bc, order, dtype)
-                g.set_kernel(variant)
+                g.set_kernel(variant, tile_cfg)
                 g.step(5, dt)
                 res.append(g.numpy())
             assert np.array_equal(res[0], res[1]), (order, bc)
+            assert np.array_equal(res[2], res[3]), (order, bc)
+
+
+@pytest.mark.parametrize("variant", [2, 3])
+@pytest.mark.parametrize("dims,shape", [(2, (19, 45)), (3, (9, 21, 70))])
+def test_exact_sum_out_of_range_falls_back(variant, dims, shape):
+    """The exact-sum stencil fixes its range from Psi at creation; a state
+    scaled far beyond it afterwards must still integrate correctly (every
+    out-of-range site takes the FP64 stencil)."""
+    psi, V = problem(shape, 91)
+    h, a, s, order = 0.3, 0.6, -1.0, 4
+    big = 100.0 * psi
+    dt = 0.2 * O.stability_bound(dims, h, a, order, float(np.max(V)), abs(s) * 1.7e4)
+    g = Integrator(psi, h, a, s, V, "dirichlet", order, "c128")
+    g.set_kernel(variant)
+    g.psi.copy_(torch.from_numpy(big).to(g.psi.device))
+    g.step(4, dt)
+    ref = O.rk4(big, h, a, s, dt, 4, V, W.BC_DIRICHLET, order)
+    compare(g.numpy(), ref, "c128")
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_bounded_wait_times_out_and_context_recovers(dtype):
+    """Every TMA barrier is made to expect 16 bytes its copy never delivers, so
+    the kernel's bounded wait runs out (no fault, no hang); the host gets
+    NLSE_ETIMEOUT once, and after the hook is removed the same context steps
+    correctly again."""
+    psi, V = problem((12, 10, 64), 17)
+    h, a, s, order = 0.3, 0.6, -1.0, 4
+    dt = stable_dt(psi.shape, h, a, s, order, V)
+    g = Integrator(psi, h, a, s, V, "msd", order, dtype)
+    g.set_kernel(1)
+    g.debug_set(L.DEBUG_SPIN_LIMIT, 200000)       # ~0.1 ms per wait
+    g.debug_set(L.DEBUG_EXTRA_TX, 16)
+    g.step(1, dt)
+    with pytest.raises(L.NLSEError) as e:
+        g.sync()
+    assert e.value.code == L.NLSE_ETIMEOUT
+    g.debug_set(L.DEBUG_EXTRA_TX, 0)
+    g.debug_set(L.DEBUG_SPIN_LIMIT, 2000000000)
+    g.psi.copy_(torch.from_numpy(psi).to(g.psi.dtype).to(g.psi.device))
+    g.step(3, dt)
+    g.sync()
+    compare(g.numpy(), O.rk4(psi, h, a, s, dt, 3, V, W.BC_MSD, order), dtype)
 
 
 def test_dt_above_bound_is_rejected():
