@@ -153,6 +153,20 @@ const char *nlse_last_error(void);
 int nlse_set_kernel(nlse_t ctx, int variant, int tile_cfg);
 
 /*
+ * Autotuner: time every tile shape of the context's tiled kernel on its own
+ * buffers (stage 1 then repeated stage-2 launches; Psi is read, never
+ * written) and keep the fastest for this context.  The choice is cached for
+ * the process per (dims, shape, dtype, order, bc, variant, V present), and
+ * appended to the text file named by the environment variable
+ * NLSE_TUNE_CACHE when it is set (later processes read it instead of
+ * timing).  Synchronises the stream.  *best_tile_cfg receives the chosen
+ * tile_cfg (-1 when nothing is tiled: 1D grids, variants 0 and 3) and
+ * *best_ms the measured stage-2 time (0 when taken from a cache); either
+ * pointer may be NULL.  Tiles never change results.
+ */
+int nlse_autotune(nlse_t ctx, int *best_tile_cfg, float *best_ms);
+
+/*
  * Test hooks for the bounded device-side waits (not needed in normal use).
  *   NLSE_DEBUG_SPIN_LIMIT  value = SM clock cycles any device-side wait may
  *                          last before the kernel gives up (default ~2e9,

@@ -50,6 +50,7 @@ SIGNATURES = {
     "nlse_last_error": (ctypes.c_char_p, []),
     "nlse_set_kernel": (_I, [_VP, _I, _I]),
     "nlse_debug_set": (_I, [_VP, _I, ctypes.c_longlong]),
+    "nlse_autotune": (_I, [_VP, ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_float)]),
 }
 
 

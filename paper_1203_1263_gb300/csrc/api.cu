@@ -5,7 +5,12 @@
 #include <math.h>
 #include <stdarg.h>
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
+
+#include <map>
+#include <mutex>
+#include <string>
 
 #include "../../include/nlse.h"
 #include "nlse_internal.h"
@@ -106,6 +111,8 @@ struct nlse_ctx {
   signed char tmap_state[4][3];   // 0 = not built, 1 = ok, -1 = layout not eligible
   long long spin_limit;           // bound on device-side waits (cycles)
   unsigned int extra_tx;          // test hook, see nlse_debug_set
+  cudaStream_t side;              // wall-shell kernels run here, concurrently with the deep kernels
+  cudaEvent_t ev_fork, ev_join;
 
   void* at(size_t off) const { return ws + off; }
   unsigned int* flag() const { return (unsigned int*)(ws + lay.status); }
@@ -115,6 +122,13 @@ struct nlse_ctx {
 };
 
 namespace {
+
+// Tile shape in use: the caller's choice, else the measured default per form
+// (32x8 for FP64, 32x16 for the FP32 forms; nlse_autotune can refine it).
+int resolved_tile(const nlse_ctx* c) {
+  if (c->tile_cfg >= 0) return c->tile_cfg;
+  return c->dtype == NLSE_C128 ? 0 : 2;
+}
 
 template <class T>
 Field<T> make_field(const nlse_ctx* c, const void* in) {
@@ -148,10 +162,13 @@ template <class T>
 cudaError_t dispatch_stage(const nlse_ctx* c, const StageArgs<T>& A, const void* tmap, cudaStream_t st) {
   LaunchCfg L;
   L.variant = c->variant;
-  L.tile_cfg = c->tile_cfg;
+  L.tile_cfg = resolved_tile(c);
   L.tmap = tmap;
   L.spin_limit = c->spin_limit;
   L.extra_tx = c->extra_tx;
+  L.side = c->side;
+  L.ev_fork = c->ev_fork;
+  L.ev_join = c->ev_join;
   switch (c->d * 10 + c->order) {
     case 12: return launch_stage<T, 1, 2>(A, L, st);
     case 14: return launch_stage<T, 1, 4>(A, L, st);
@@ -168,7 +185,7 @@ cudaError_t dispatch_stage(const nlse_ctx* c, const StageArgs<T>& A, const void*
 const CUtensorMap* stage_tmap(const nlse_ctx* cc, int buf, const void* ptr) {
   nlse_ctx* c = const_cast<nlse_ctx*>(cc);
   if (c->d != 3 || (c->variant != 1 && c->variant != 2)) return nullptr;
-  const int tc = (c->tile_cfg < 0) ? 0 : c->tile_cfg;
+  const int tc = resolved_tile(c);
   signed char& st = c->tmap_state[tc][buf];
   if (st == 0) {
     st = -1;
@@ -191,9 +208,9 @@ const CUtensorMap* stage_tmap(const nlse_ctx* cc, int buf, const void* ptr) {
   return st == 1 ? &c->tmaps[tc][buf] : nullptr;
 }
 
-// One RK4 step = four fused stages (Eq. RK4_GPU): Psi -> Psi_tmp -> Psi_out -> Psi_tmp -> Psi.
+// Stage s (1..4) of Eq. RK4_GPU: Psi -> Psi_tmp -> Psi_out -> Psi_tmp -> Psi.
 template <class T>
-cudaError_t launch_step(const nlse_ctx* c, double dt, cudaStream_t st) {
+cudaError_t launch_one_stage(const nlse_ctx* c, int s, double dt, cudaStream_t st) {
   using C = typename T::C;
   using R = typename T::R;
   const bool mix = (c->dtype == NLSE_C64_ACC64);
@@ -205,23 +222,37 @@ cudaError_t launch_step(const nlse_ctx* c, double dt, cudaStream_t st) {
   const int inbuf[4] = {0, 1, 2, 1};
   C* outs[4] = {ptmp, pout, ptmp, nullptr};
   const double dtc[4] = {dt / 2.0, dt / 2.0, dt, dt / 6.0};
-  for (int s = 0; s < 4; ++s) {
-    StageArgs<T> A;
-    memset(&A, 0, sizeof(A));
-    A.f = make_field<T>(c, in[s]);
-    A.psin = psin;
-    A.ktot = ktot;
-    A.out = outs[s];
-    A.master = (typename T::M*)c->psi;
-    A.n32 = mix ? (C*)c->at(c->lay.pn32) : nullptr;
-    A.dtc = R(dtc[s]);
-    A.dt6 = dt / 6.0;
-    A.stage = s + 1;
-    A.flag = c->flag();
-    cudaError_t e = dispatch_stage<T>(c, A, stage_tmap(c, inbuf[s], in[s]), st);
+  const int i = s - 1;
+  StageArgs<T> A;
+  memset(&A, 0, sizeof(A));
+  A.f = make_field<T>(c, in[i]);
+  A.psin = psin;
+  A.ktot = ktot;
+  A.out = outs[i];
+  A.master = (typename T::M*)c->psi;
+  A.n32 = mix ? (C*)c->at(c->lay.pn32) : nullptr;
+  A.dtc = R(dtc[i]);
+  A.dt6 = dt / 6.0;
+  A.stage = s;
+  A.flag = c->flag();
+  return dispatch_stage<T>(c, A, stage_tmap(c, inbuf[i], in[i]), st);
+}
+
+template <class T>
+cudaError_t launch_step(const nlse_ctx* c, double dt, cudaStream_t st) {
+  for (int s = 1; s <= 4; ++s) {
+    cudaError_t e = launch_one_stage<T>(c, s, dt, st);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
+}
+
+cudaError_t launch_stage_any(const nlse_ctx* c, int s, double dt, cudaStream_t st) {
+  switch (c->dtype) {
+    case NLSE_C128: return launch_one_stage<P64>(c, s, dt, st);
+    case NLSE_C64: return launch_one_stage<P32>(c, s, dt, st);
+    default: return launch_one_stage<PMix>(c, s, dt, st);
+  }
 }
 
 cudaError_t launch_step_any(const nlse_ctx* c, double dt, cudaStream_t st) {
@@ -344,7 +375,7 @@ int nlse_create(nlse_t* out, int dims, const int64_t* N, double h, double a, dou
   c->stream = (cudaStream_t)stream;
   c->ws = (char*)workspace;
   c->lay = L;
-  c->variant = 1;
+  c->variant = (dtype == NLSE_C128) ? 2 : 1;   // FP64: exact-sum stencil
   c->tile_cfg = -1;
   c->spin_limit = kSpinLimit;
   c->graph_dt = -1.0;
@@ -356,6 +387,11 @@ int nlse_create(nlse_t* out, int dims, const int64_t* N, double h, double a, dou
     if (e == cudaSuccess) e = cudaMemcpyAsync(&bits, c->vbits(), sizeof(bits), cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     memcpy(&c->vmax, &bits, sizeof(double));
+  }
+  if (e == cudaSuccess && dims >= 2) {
+    e = cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming);
   }
   // Exact-sum stencil scale: operands must satisfy |v| < 2^(54 - F); take the
   // largest component of Psi0 with 8x headroom for growth.
@@ -374,7 +410,7 @@ int nlse_create(nlse_t* out, int dims, const int64_t* N, double h, double a, dou
     }
   }
   if (e != cudaSuccess) {
-    delete c;
+    nlse_destroy(c);
     return cuda_fail(e, "nlse_create");
   }
   *out = c;
@@ -479,6 +515,101 @@ int nlse_energy(nlse_t c, double* out_host) {
   return NLSE_OK;
 }
 
+namespace {
+std::mutex g_tune_mu;
+std::map<std::string, int> g_tune;   // process-wide cache: context key -> tile_cfg
+
+std::string tune_key(const nlse_ctx* c) {
+  char b[160];
+  snprintf(b, sizeof(b), "d%d n%lldx%lldx%lld t%d o%d bc%d v%d V%d", c->d, (long long)c->n[0], (long long)c->n[1],
+           (long long)c->n[2], c->dtype, c->order, c->bc, c->variant, c->V ? 1 : 0);
+  return b;
+}
+
+bool tune_file_lookup(const std::string& key, int* cfg) {
+  const char* path = getenv("NLSE_TUNE_CACHE");
+  if (!path) return false;
+  FILE* f = fopen(path, "r");
+  if (!f) return false;
+  char line[256];
+  bool found = false;
+  while (fgets(line, sizeof(line), f)) {
+    char* eq = strrchr(line, '=');
+    if (!eq) continue;
+    *eq = 0;
+    if (key == line) { *cfg = atoi(eq + 1); found = true; }
+  }
+  fclose(f);
+  return found;
+}
+
+void tune_file_store(const std::string& key, int cfg) {
+  const char* path = getenv("NLSE_TUNE_CACHE");
+  if (!path) return;
+  FILE* f = fopen(path, "a");
+  if (!f) return;
+  fprintf(f, "%s=%d\n", key.c_str(), cfg);
+  fclose(f);
+}
+}  // namespace
+
+int nlse_autotune(nlse_t c, int* best_tile_cfg, float* best_ms) {
+  if (!c) return fail(NLSE_EINVAL, "NULL context");
+  if (c->d == 1 || c->variant == 0 || c->variant == 3) {   // nothing tiled to tune
+    if (best_tile_cfg) *best_tile_cfg = -1;
+    if (best_ms) *best_ms = 0.f;
+    return NLSE_OK;
+  }
+  const std::string key = tune_key(c);
+  int cfg = -1;
+  {
+    std::lock_guard<std::mutex> g(g_tune_mu);
+    auto it = g_tune.find(key);
+    if (it != g_tune.end()) cfg = it->second;
+  }
+  float best = 0.f;
+  if (cfg < 0 && tune_file_lookup(key, &cfg)) {
+    std::lock_guard<std::mutex> g(g_tune_mu);
+    g_tune[key] = cfg;
+  }
+  if (cfg < 0) {
+    // time stage 2 (the heaviest stage) for every tile; stage 1 fills its inputs.
+    // Neither stage writes Psi.
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const int saved = c->tile_cfg;
+    best = 1e30f;
+    cudaError_t e = cudaSuccess;
+    if (c->dtype == NLSE_C64_ACC64)
+      e = launch_round_master((const double2*)c->psi, (float2*)c->at(c->lay.pn32), c->total, c->stream);
+    for (int t = 0; t < 4 && e == cudaSuccess; ++t) {
+      c->tile_cfg = t;
+      e = launch_stage_any(c, 1, 1e-12, c->stream);
+      if (e == cudaSuccess) e = launch_stage_any(c, 2, 1e-12, c->stream);
+      if (e == cudaSuccess) e = cudaEventRecord(e0, c->stream);
+      for (int r = 0; r < 3 && e == cudaSuccess; ++r) e = launch_stage_any(c, 2, 1e-12, c->stream);
+      if (e == cudaSuccess) e = cudaEventRecord(e1, c->stream);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      float ms = 0.f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      if (e == cudaSuccess && ms / 3 < best) { best = ms / 3; cfg = t; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c->tile_cfg = saved;
+    if (e != cudaSuccess) return cuda_fail(e, "autotune");
+    std::lock_guard<std::mutex> g(g_tune_mu);
+    g_tune[key] = cfg;
+    tune_file_store(key, cfg);
+  }
+  c->tile_cfg = cfg;
+  drop_graph(c);
+  if (best_tile_cfg) *best_tile_cfg = cfg;
+  if (best_ms) *best_ms = best;
+  return NLSE_OK;
+}
+
 int nlse_debug_set(nlse_t c, int key, long long value) {
   if (!c) return fail(NLSE_EINVAL, "NULL context");
   switch (key) {
@@ -508,6 +639,9 @@ int nlse_destroy(nlse_t c) {
   if (!c) return NLSE_OK;
   drop_graph(c);
   if (c->cap) cudaStreamDestroy(c->cap);
+  if (c->side) cudaStreamDestroy(c->side);
+  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+  if (c->ev_join) cudaEventDestroy(c->ev_join);
   delete c;
   return NLSE_OK;
 }

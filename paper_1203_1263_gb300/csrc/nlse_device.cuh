@@ -263,6 +263,27 @@ __device__ __forceinline__ longlong2 exact_s2_wall(const Field<T>& f, const Acc&
   return make_longlong2(sx, sy);
 }
 
+// int64 -> double with IEEE-754 round-to-nearest-even, on the integer pipe
+// (the hardware conversion runs on the FP64 pipe, GB300's scarcest unit).
+// Exact for |v| < 2^53; one correctly rounded result otherwise.
+__device__ __forceinline__ double i2d_rn(long long v) {
+  if (v == 0) return 0.0;
+  const unsigned long long sgn = (unsigned long long)v & 0x8000000000000000ull;
+  unsigned long long u = sgn ? 0ull - (unsigned long long)v : (unsigned long long)v;
+  int e = 63 - __clzll(u);                 // position of the leading one
+  unsigned long long m;
+  if (e <= 52) {
+    m = u << (52 - e);
+  } else {
+    const int sh = e - 52;
+    m = u >> sh;
+    const unsigned long long rem = u & ((1ull << sh) - 1), half = 1ull << (sh - 1);
+    if (rem > half || (rem == half && (m & 1ull))) ++m;
+    if (m == (1ull << 53)) { m >>= 1; ++e; }
+  }
+  return __longlong_as_double((long long)(sgn | ((unsigned long long)(e + 1023) << 52) | (m & 0x000FFFFFFFFFFFFFull)));
+}
+
 template <class T, int D, int ORDER, class Acc>
 __device__ __forceinline__ double2 a_lap_exact(const Field<T>& f, const Acc& acc, const int* idx, int64_t c,
                                                double2 pc, double Nc) {
@@ -495,7 +516,29 @@ struct LaunchCfg {
   const void* tmap;        // CUtensorMap* of A.f.in for the tile's box, or nullptr
   long long spin_limit;    // bound on any device-side wait, in SM clock cycles
   unsigned int extra_tx;   // test hook: extra bytes every TMA barrier waits for (0 in normal use)
+  cudaStream_t side;       // if set, the wall-shell kernel runs on this stream, concurrently with the
+  cudaEvent_t ev_fork;     //   deep-interior kernel (fork after ev_fork on the main stream, join on ev_join)
+  cudaEvent_t ev_join;
 };
+
+// Launch the deep-interior part and the wall-shell part of one stage; with a
+// side stream they run concurrently (they write disjoint sites and read the
+// same stage input).
+template <class DeepFn, class ShellFn>
+cudaError_t launch_deep_and_shell(const LaunchCfg& L, cudaStream_t stream, bool deep, DeepFn&& run_deep,
+                                  ShellFn&& run_shell) {
+  cudaError_t e = cudaSuccess;
+  if (L.side && deep) {
+    if ((e = cudaEventRecord(L.ev_fork, stream)) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(L.side, L.ev_fork, 0)) != cudaSuccess) return e;
+    if ((e = run_shell(L.side)) != cudaSuccess) return e;
+    if ((e = cudaEventRecord(L.ev_join, L.side)) != cudaSuccess) return e;
+    if ((e = run_deep(stream)) != cudaSuccess) return e;
+    return cudaStreamWaitEvent(stream, L.ev_join, 0);
+  }
+  if (deep && (e = run_deep(stream)) != cudaSuccess) return e;
+  return run_shell(stream);
+}
 
 // Host-visible launch entry points (defined in stage_*.cu).
 template <class T, int D, int ORDER>

@@ -15,18 +15,15 @@ cudaError_t launch_stage(const StageArgs<T>& A, const LaunchCfg& L, cudaStream_t
     return launch_generic<T, D, ORDER>(A, stream);
   }
   // tiled: deep interior + the wall shell
-  cudaError_t e = cudaSuccess;
-  if (has_deep(D, A.f.m)) {
-    if constexpr (fp64) {
-      if (exact) e = launch2d_tiled<T, ORDER, true>(A, L.tile_cfg, stream);
-      else e = launch2d_tiled<T, ORDER>(A, L.tile_cfg, stream);
-    } else {
-      e = launch2d_tiled<T, ORDER>(A, L.tile_cfg, stream);
-    }
-    if (e != cudaSuccess) return e;
-  }
-  if constexpr (fp64) if (exact) return launch_shell<T, D, ORDER, true>(A, stream);
-  return launch_shell<T, D, ORDER>(A, stream);
+  auto deep = [&](cudaStream_t st) -> cudaError_t {
+    if constexpr (fp64) if (exact) return launch2d_tiled<T, ORDER, true>(A, L.tile_cfg, st);
+    return launch2d_tiled<T, ORDER>(A, L.tile_cfg, st);
+  };
+  auto shell = [&](cudaStream_t st) -> cudaError_t {
+    if constexpr (fp64) if (exact) return launch_shell<T, D, ORDER, true>(A, st);
+    return launch_shell<T, D, ORDER>(A, st);
+  };
+  return launch_deep_and_shell(L, stream, has_deep(D, A.f.m), deep, shell);
 }
 
 #define INST(T, O) template cudaError_t launch_stage<T, 2, O>(const StageArgs<T>&, const LaunchCfg&, cudaStream_t);

@@ -20,18 +20,17 @@ cudaError_t launch_stage(const StageArgs<T>& A, const LaunchCfg& L, cudaStream_t
     return launch_generic<T, D, ORDER>(A, stream);
   }
   // tiled: deep interior (TMA-fed when the layout allows) + the wall shell
-  cudaError_t e = cudaSuccess;
-  if (has_deep(D, A.f.m)) {
+  auto deep = [&](cudaStream_t st) -> cudaError_t {
     if constexpr (fp64) {
-      if (exact) e = L.tmap ? launch3d_tma<T, ORDER, true>(A, L, stream) : launch3d_tiled<T, ORDER, true>(A, L.tile_cfg, stream);
-      else e = L.tmap ? launch3d_tma<T, ORDER, false>(A, L, stream) : launch3d_tiled<T, ORDER>(A, L.tile_cfg, stream);
-    } else {
-      e = L.tmap ? launch3d_tma<T, ORDER, false>(A, L, stream) : launch3d_tiled<T, ORDER>(A, L.tile_cfg, stream);
+      if (exact) return L.tmap ? launch3d_tma<T, ORDER, true>(A, L, st) : launch3d_tiled<T, ORDER, true>(A, L.tile_cfg, st);
     }
-    if (e != cudaSuccess) return e;
-  }
-  if constexpr (fp64) if (exact) return launch_shell<T, D, ORDER, true>(A, stream);
-  return launch_shell<T, D, ORDER>(A, stream);
+    return L.tmap ? launch3d_tma<T, ORDER, false>(A, L, st) : launch3d_tiled<T, ORDER>(A, L.tile_cfg, st);
+  };
+  auto shell = [&](cudaStream_t st) -> cudaError_t {
+    if constexpr (fp64) if (exact) return launch_shell<T, D, ORDER, true>(A, st);
+    return launch_shell<T, D, ORDER>(A, st);
+  };
+  return launch_deep_and_shell(L, stream, has_deep(D, A.f.m), deep, shell);
 }
 
 }  // namespace nlse

@@ -7,16 +7,20 @@
 
 namespace nlse {
 
-template <class T, int D, int ORDER, bool EXACT>
+// I = index type of the site decode: uint32_t whenever the count fits
+// (64-bit integer division is a long software sequence on the GPU).
+template <class T, int D, int ORDER, bool EXACT, class I>
 __global__ void __launch_bounds__(256) k_stage_generic(const StageArgs<T> A) {
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= A.f.ninterior) return;
+  const int64_t t64 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t64 >= A.f.ninterior) return;
   int idx[D];
-  int64_t rem = t, c = 0;
+  I rem = I(t64);
+  int64_t c = 0;
 #pragma unroll
   for (int k = D - 1; k >= 0; --k) {
-    const int64_t q = rem % A.f.m[k];
-    rem /= A.f.m[k];
+    const I mk = I(A.f.m[k]);
+    const I q = rem % mk;
+    rem /= mk;
     idx[k] = int(q) + 1;
     c += idx[k] * A.f.st[k];
   }
@@ -35,8 +39,8 @@ __global__ void __launch_bounds__(256) k_stage_generic(const StageArgs<T> A) {
 //   {i_0 in the c_0 outer layers} x a_1 x a_2
 //   + d_0 x {i_1 in the c_1 outer layers} x a_2 + d_0 x d_1 x {c_2 outer layers}.
 // ---------------------------------------------------------------------------
-template <class T, int D>
-__device__ __forceinline__ int64_t shell_decode(const Field<T>& f, int64_t t, int* idx) {
+template <class T, int D, class I>
+__device__ __forceinline__ int64_t shell_decode(const Field<T>& f, I t, int* idx) {
   int a[3], d[3], c[3];
 #pragma unroll
   for (int k = 0; k < D; ++k) {
@@ -48,38 +52,38 @@ __device__ __forceinline__ int64_t shell_decode(const Field<T>& f, int64_t t, in
   if constexpr (D == 1) {
     idx[0] = outer(0, int(t));
   } else if constexpr (D == 2) {
-    const int64_t F0 = (int64_t)c[0] * a[1];
+    const I F0 = I(c[0]) * I(a[1]);
     if (t < F0) {
-      idx[0] = outer(0, int(t / a[1]));
-      idx[1] = 1 + int(t % a[1]);
+      idx[0] = outer(0, int(t / I(a[1])));
+      idx[1] = 1 + int(t % I(a[1]));
     } else {
       t -= F0;
-      idx[0] = 2 + int(t / c[1]);
-      idx[1] = outer(1, int(t % c[1]));
+      idx[0] = 2 + int(t / I(c[1]));
+      idx[1] = outer(1, int(t % I(c[1])));
     }
   } else {
-    const int64_t F0 = (int64_t)c[0] * a[1] * a[2];
-    const int64_t F1 = (int64_t)d[0] * c[1] * a[2];
+    const I F0 = I(c[0]) * I(a[1]) * I(a[2]);
+    const I F1 = I(d[0]) * I(c[1]) * I(a[2]);
     if (t < F0) {
-      const int64_t pa = (int64_t)a[1] * a[2];
+      const I pa = I(a[1]) * I(a[2]);
       idx[0] = outer(0, int(t / pa));
-      const int64_t r = t % pa;
-      idx[1] = 1 + int(r / a[2]);
-      idx[2] = 1 + int(r % a[2]);
+      const I r = t % pa;
+      idx[1] = 1 + int(r / I(a[2]));
+      idx[2] = 1 + int(r % I(a[2]));
     } else if (t < F0 + F1) {
       t -= F0;
-      const int64_t pa = (int64_t)c[1] * a[2];
+      const I pa = I(c[1]) * I(a[2]);
       idx[0] = 2 + int(t / pa);
-      const int64_t r = t % pa;
-      idx[1] = outer(1, int(r / a[2]));
-      idx[2] = 1 + int(r % a[2]);
+      const I r = t % pa;
+      idx[1] = outer(1, int(r / I(a[2])));
+      idx[2] = 1 + int(r % I(a[2]));
     } else {
       t -= F0 + F1;
-      const int64_t pa = (int64_t)d[1] * c[2];
+      const I pa = I(d[1]) * I(c[2]);
       idx[0] = 2 + int(t / pa);
-      const int64_t r = t % pa;
-      idx[1] = 2 + int(r / c[2]);
-      idx[2] = outer(2, int(r % c[2]));
+      const I r = t % pa;
+      idx[1] = 2 + int(r / I(c[2]));
+      idx[2] = outer(2, int(r % I(c[2])));
     }
   }
   int64_t s = 0;
@@ -103,12 +107,12 @@ inline bool has_deep(int D, const int* m) {
   return true;
 }
 
-template <class T, int D, int ORDER, bool EXACT>
+template <class T, int D, int ORDER, bool EXACT, class I>
 __global__ void __launch_bounds__(256) k_stage_shell(const StageArgs<T> A, int64_t nshell) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= nshell) return;
   int idx[D];
-  const int64_t c = shell_decode<T, D>(A.f, t, idx);
+  const int64_t c = shell_decode<T, D, I>(A.f, I(t), idx);
   const GAcc<T, D> acc(A.f, c);
   process_site<T, D, ORDER, EXACT>(A, acc, idx, c);
 }
@@ -118,7 +122,9 @@ cudaError_t launch_shell(const StageArgs<T>& A, cudaStream_t stream) {
   const int64_t ns = shell_count(D, A.f.m);
   if (ns <= 0) return cudaSuccess;
   const int threads = 256;
-  k_stage_shell<T, D, ORDER, EXACT><<<dim3((unsigned)((ns + threads - 1) / threads)), threads, 0, stream>>>(A, ns);
+  const dim3 grid((unsigned)((ns + threads - 1) / threads));
+  if (A.f.ninterior < (int64_t(1) << 31)) k_stage_shell<T, D, ORDER, EXACT, uint32_t><<<grid, threads, 0, stream>>>(A, ns);
+  else k_stage_shell<T, D, ORDER, EXACT, uint64_t><<<grid, threads, 0, stream>>>(A, ns);
   return cudaGetLastError();
 }
 
@@ -127,7 +133,10 @@ cudaError_t launch_generic(const StageArgs<T>& A, cudaStream_t stream) {
   if (A.f.ninterior <= 0) return cudaSuccess;
   const int threads = 256;
   const int64_t blocks = (A.f.ninterior + threads - 1) / threads;
-  k_stage_generic<T, D, ORDER, EXACT><<<dim3((unsigned)blocks), threads, 0, stream>>>(A);
+  if (A.f.ninterior < (int64_t(1) << 31))
+    k_stage_generic<T, D, ORDER, EXACT, uint32_t><<<dim3((unsigned)blocks), threads, 0, stream>>>(A);
+  else
+    k_stage_generic<T, D, ORDER, EXACT, uint64_t><<<dim3((unsigned)blocks), threads, 0, stream>>>(A);
   return cudaGetLastError();
 }
 

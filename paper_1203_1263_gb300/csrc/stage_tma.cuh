@@ -212,6 +212,198 @@ __global__ void __launch_bounds__(TX* TYT) k_stage3d_tma(const StageArgs<T> A, c
   }
 }
 
+// ---------------------------------------------------------------------------
+// FP64 exact-sum variant.  Each landed plane is converted once to fixed point
+// (fix2) into a second ring that holds planes z-2 .. z+3, one plane ahead of
+// use, so the per-plane barrier that releases slots also orders the
+// conversion before the reads.  The FP64 ring only holds planes between
+// their landing and their conversion (P + 1 slots); the centre values in
+// FP64 come with the prefetched pointwise operands.  The stencil sums become
+// exact integers; i2d_rn turns them into FP64 on the integer pipe.
+// ---------------------------------------------------------------------------
+template <class T, int ORDER, int S, int TX, int TYT, int RY, int P>
+__global__ void __launch_bounds__(TX* TYT) k_stage3d_tma_exact(const StageArgs<T> A,
+                                                              const __grid_constant__ CUtensorMap tm, int zc,
+                                                              long long spin_limit, uint32_t extra_tx) {
+  static_assert(std::is_same<typename T::R, double>::value, "FP64 only");
+  constexpr int TY = TYT * RY;
+  using G = TmaGeom<TX, TY, double2>;
+  constexpr int RD = P + 1;                        // FP64 landing slots
+  constexpr int RF = 6;                            // fixed-point planes z-2 .. z+3
+  constexpr int NT = TX * TYT, NPER = (G::PS + NT - 1) / NT;
+  extern __shared__ __align__(128) unsigned char tma_smem[];
+  unsigned char* dslots = tma_smem;
+  longlong2* fring = reinterpret_cast<longlong2*>(tma_smem + RD * G::kSlot);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(tma_smem + (RD + RF) * G::kSlot);
+  const Field<T>& f = A.f;
+  const int nz = f.n[0], ny = f.n[1], nx = f.n[2];
+  const int tid = threadIdx.y * TX + threadIdx.x;
+  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+  const int zb = 1 + blockIdx.z * zc;
+  const int ze = min(zb + zc, nz - 1);
+  const int jb = zb - 2, jl = ze + 1;
+  const int64_t plane = (int64_t)ny * nx;
+  const bool with_v = f.V != nullptr;
+  const int F = f.F;
+
+  if (tid == 0) {
+    for (int s = 0; s < RD; ++s) mbar_init(smem_u32(bars + s), 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  int islot = 0, issued = jb - 1;
+  auto issue = [&](int j) {
+    mbar_expect_tx(smem_u32(bars + islot), G::kBytes + extra_tx);
+    tma_load_3d(smem_u32(dslots + islot * G::kSlot), &tm, 2 * (x0 - 2), y0 - 2, j, smem_u32(bars + islot));
+    islot = (islot + 1 == RD) ? 0 : islot + 1;
+    issued = j;
+  };
+  if (tid == 0)
+    for (int j = jb; j < jb + RD && j <= jl; ++j) issue(j);
+
+  int wslot = 0, fslot = 0;
+  uint32_t wpar = 0;
+  bool late = false;
+  // land plane j, convert it into the fixed ring; its FP64 slot is free after the next barrier
+  auto land_and_convert = [&](int j) {
+    late |= !mbar_wait_bounded(smem_u32(bars + wslot), wpar, spin_limit);
+    const double2* src = reinterpret_cast<const double2*>(dslots + wslot * G::kSlot);
+    longlong2* dst = fring + fslot * G::PS;
+#pragma unroll
+    for (int i = 0; i < NPER; ++i) {
+      const int e = tid + i * NT;
+      if (e < G::PS) dst[e] = fix2(src[e], F);
+    }
+    if (++wslot == RD) { wslot = 0; wpar ^= 1u; }
+    fslot = (fslot + 1 == RF) ? 0 : fslot + 1;
+  };
+
+  const int gx = x0 + threadIdx.x;
+  int gy[RY], o[RY];
+  bool deep[RY];
+  int64_t col[RY];
+#pragma unroll
+  for (int r = 0; r < RY; ++r) {
+    gy[r] = y0 + threadIdx.y + r * TYT;
+    o[r] = (threadIdx.y + r * TYT + 2) * G::W + threadIdx.x + 2;
+    deep[r] = gx >= 2 && gx <= nx - 3 && gy[r] >= 2 && gy[r] <= ny - 3;
+    col[r] = (int64_t)gy[r] * nx + gx;
+  }
+
+  // planes jb .. jb+4 (z-2 .. z+2 of the first plane) into the fixed ring
+  for (int j = jb; j <= jb + 4; ++j) {
+    land_and_convert(j);
+    __syncthreads();
+    if (tid == 0 && issued < jl) issue(issued + 1);
+  }
+  int fz = 0;   // fixed slot of plane z-2
+
+  PointVals<T> pv_next[RY];
+  double2 pc_next[RY];
+#pragma unroll
+  for (int r = 0; r < RY; ++r)
+    if (deep[r]) {
+      pv_next[r] = load_point<T, S>(A, zb * plane + col[r], with_v);
+      pc_next[r] = f.in[zb * plane + col[r]];
+    }
+  bool aborted = false;
+  for (int z = zb; z < ze; ++z) {
+    PointVals<T> pv[RY];
+    double2 pcs[RY];
+#pragma unroll
+    for (int r = 0; r < RY; ++r) {
+      pv[r] = pv_next[r];
+      pcs[r] = pc_next[r];
+      if (deep[r] && z + 1 < ze) {
+        pv_next[r] = load_point<T, S>(A, (z + 1) * plane + col[r], with_v);
+        pc_next[r] = f.in[(z + 1) * plane + col[r]];
+      }
+    }
+    if (z + 3 <= jl) land_and_convert(z + 3);   // one plane ahead of use
+    const bool deep_z = z >= 2 && z <= nz - 3;
+    const longlong2* pl[5];
+#pragma unroll
+    for (int d = 0; d < 5; ++d) {
+      const int q = fz + d;
+      pl[d] = fring + (q >= RF ? q - RF : q) * G::PS;
+    }
+#pragma unroll
+    for (int r = 0; r < RY; ++r) {
+      if (!(deep[r] && deep_z) || late) continue;
+      const int64_t c = z * plane + col[r];
+      const int oo = o[r];
+      const longlong2 cc = pl[2][oo];
+      const longlong2 xm = pl[2][oo - 1], xp = pl[2][oo + 1], ym = pl[2][oo - G::W], yp = pl[2][oo + G::W];
+      const longlong2 zm = pl[1][oo], zp = pl[3][oo];
+      bool bad = fbad(cc) | fbad(xm) | fbad(xp) | fbad(ym) | fbad(yp) | fbad(zm) | fbad(zp);
+      // axis order 0 (z), 1 (y), 2 (x) as in a_lap_exact
+      long long s1x = (zp.x + zm.x) + (yp.x + ym.x) + (xp.x + xm.x);
+      long long s1y = (zp.y + zm.y) + (yp.y + ym.y) + (xp.y + xm.y);
+      long long Sx, Sy;
+      if constexpr (ORDER == 2) {
+        Sx = s1x - 6 * cc.x;
+        Sy = s1y - 6 * cc.y;
+      } else {
+        const longlong2 xm2 = pl[2][oo - 2], xp2 = pl[2][oo + 2], ym2 = pl[2][oo - 2 * G::W],
+                        yp2 = pl[2][oo + 2 * G::W], zm2 = pl[0][oo], zp2 = pl[4][oo];
+        bad |= fbad(xm2) | fbad(xp2) | fbad(ym2) | fbad(yp2) | fbad(zm2) | fbad(zp2);
+        const long long s2x = (zm2.x + zp2.x) + (ym2.x + yp2.x) + (xm2.x + xp2.x);
+        const long long s2y = (zm2.y + zp2.y) + (ym2.y + yp2.y) + (xm2.y + xp2.y);
+        Sx = 16 * s1x - s2x - 90 * cc.x;
+        Sy = 16 * s1y - s2y - 90 * cc.y;
+      }
+      const double2 pc = pcs[r];
+      const double Nc = fma(f.s, norm2(pc), -pv[r].v);
+      double2 aL;
+      if (!bad) {
+        aL = {f.cLF * i2d_rn(Sx), f.cLF * i2d_rn(Sy)};
+      } else {   // an operand out of the fixed-point range: the FP64 stencil from global memory
+        const int idx[3] = {z, gy[r], gx};
+        const GAcc<T, 3> ga(f, c);
+        aL = a_lap_slow<T, 3, ORDER>(f, ga, idx, c, pc, Nc);
+      }
+      rk_apply<T, S>(A, c, {-fma(Nc, pc.y, aL.y), fma(Nc, pc.x, aL.x)}, pv[r]);
+    }
+    if (__syncthreads_or(late)) {
+      aborted = true;
+      break;
+    }
+    fz = (fz + 1 == RF) ? 0 : fz + 1;
+    if (tid == 0 && issued < jl) issue(issued + 1);
+  }
+  if (aborted && tid == 0) {
+    atomicOr(A.flag, kFlagTimeout);
+    for (int j = max(jb, issued - RD + 1); j <= issued; ++j) {
+      const int q = j - jb;
+      mbar_wait_bounded(smem_u32(bars + q % RD), uint32_t((q / RD) & 1), spin_limit);
+    }
+  }
+}
+
+template <class T, int ORDER, int S, int TX, int TYT, int RY, int P>
+cudaError_t launch3d_tma_exact_shape(const StageArgs<T>& A, const CUtensorMap* tm, long long spin_limit,
+                                     uint32_t extra_tx, cudaStream_t stream) {
+  constexpr int TY = TYT * RY;
+  using G = TmaGeom<TX, TY, double2>;
+  const int nz = A.f.n[0], ny = A.f.n[1], nx = A.f.n[2];
+  const int tiles = ((nx + TX - 1) / TX) * ((ny + TY - 1) / TY);
+  const int planes = nz - 2;
+  int nzc = (152 * 8 + tiles - 1) / tiles;
+  if (nzc > planes) nzc = planes;
+  if (nzc < 1) nzc = 1;
+  const int zc = (planes + nzc - 1) / nzc;
+  nzc = (planes + zc - 1) / zc;
+  const size_t smem = (P + 1 + 6) * G::kSlot + (P + 1) * sizeof(uint64_t);
+  auto kern = k_stage3d_tma_exact<T, ORDER, S, TX, TYT, RY, P>;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  dim3 grid((nx + TX - 1) / TX, (ny + TY - 1) / TY, nzc);
+  kern<<<grid, dim3(TX, TYT), smem, stream>>>(A, *tm, zc, spin_limit, extra_tx);
+  return cudaGetLastError();
+}
+
 template <class T, int ORDER, int S, int TX, int TYT, int RY, int P, bool EXACT>
 cudaError_t launch3d_tma_shape(const StageArgs<T>& A, const CUtensorMap* tm, long long spin_limit,
                                uint32_t extra_tx, cudaStream_t stream) {
@@ -239,6 +431,14 @@ cudaError_t launch3d_tma_shape(const StageArgs<T>& A, const CUtensorMap* tm, lon
 template <class T, int ORDER, int S, bool EXACT>
 cudaError_t launch3d_tma_stage(const StageArgs<T>& A, const LaunchCfg& L, cudaStream_t stream) {
   const CUtensorMap* tm = static_cast<const CUtensorMap*>(L.tmap);
+  if constexpr (EXACT) {
+    switch (L.tile_cfg) {
+      case 1: return launch3d_tma_exact_shape<T, ORDER, S, 64, 4, 1, 2>(A, tm, L.spin_limit, L.extra_tx, stream);
+      case 2: return launch3d_tma_exact_shape<T, ORDER, S, 32, 8, 2, 2>(A, tm, L.spin_limit, L.extra_tx, stream);
+      case 3: return launch3d_tma_exact_shape<T, ORDER, S, 64, 4, 2, 2>(A, tm, L.spin_limit, L.extra_tx, stream);
+      default: return launch3d_tma_exact_shape<T, ORDER, S, 32, 8, 1, 2>(A, tm, L.spin_limit, L.extra_tx, stream);
+    }
+  }
   switch (L.tile_cfg) {   // the tile shapes of tma_tile_shape()
     case 1: return launch3d_tma_shape<T, ORDER, S, 64, 4, 1, 2, EXACT>(A, tm, L.spin_limit, L.extra_tx, stream);
     case 2: return launch3d_tma_shape<T, ORDER, S, 32, 8, 2, 2, EXACT>(A, tm, L.spin_limit, L.extra_tx, stream);

@@ -108,6 +108,13 @@ class Integrator:
     def set_kernel(self, variant: int, tile_cfg: int = -1) -> None:
         L.check(self.lib.nlse_set_kernel(self.ctx, int(variant), int(tile_cfg)))
 
+    def autotune(self):
+        """Pick the fastest tile shape for this problem (see nlse_autotune); returns (tile_cfg, ms)."""
+        cfg = ctypes.c_int()
+        ms = ctypes.c_float()
+        L.check(self.lib.nlse_autotune(self.ctx, ctypes.byref(cfg), ctypes.byref(ms)))
+        return cfg.value, ms.value
+
     def debug_set(self, key: int, value: int) -> None:
         """Test hook for the bounded device-side waits (see nlse_debug_set)."""
         L.check(self.lib.nlse_debug_set(self.ctx, int(key), int(value)))

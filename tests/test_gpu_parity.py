@@ -211,6 +211,31 @@ def test_bounded_wait_times_out_and_context_recovers(dtype):
     compare(g.numpy(), O.rk4(psi, h, a, s, dt, 3, V, W.BC_MSD, order), dtype)
 
 
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_autotune_picks_a_tile_and_keeps_results(dtype, tmp_path, monkeypatch):
+    """The autotuner times the tile shapes on the context's own buffers without
+    touching Psi, keeps one, and a second process-level lookup comes from the
+    cache; the integration result is bit-for-bit the default's."""
+    monkeypatch.setenv("NLSE_TUNE_CACHE", str(tmp_path / "tune.txt"))
+    psi, V = problem((14, 30, 72), 23)
+    h, a, s, order = 0.3, 0.6, -1.0, 4
+    dt = stable_dt(psi.shape, h, a, s, order, V)
+    g0 = Integrator(psi, h, a, s, V, "msd", order, dtype)
+    g0.step(6, dt)
+    ref = g0.numpy()
+    g = Integrator(psi, h, a, s, V, "msd", order, dtype)
+    before = g.numpy()
+    cfg, ms = g.autotune()
+    assert cfg in (0, 1, 2, 3) and ms > 0
+    assert np.array_equal(before, g.numpy())          # Psi untouched by tuning
+    g.step(6, dt)
+    assert np.array_equal(ref, g.numpy())
+    g2 = Integrator(psi, h, a, s, V, "msd", order, dtype)
+    cfg2, ms2 = g2.autotune()
+    assert cfg2 == cfg and ms2 == 0.0                 # served from the cache
+    assert (tmp_path / "tune.txt").read_text().count("=") >= 1
+
+
 def test_dt_above_bound_is_rejected():
     psi, V = problem((10, 10), 4)
     g = Integrator(psi, 0.2, 1.0, 1.0, V, "dirichlet", 4, "c128")
