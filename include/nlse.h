@@ -167,6 +167,34 @@ int nlse_set_kernel(nlse_t ctx, int variant, int tile_cfg);
 int nlse_autotune(nlse_t ctx, int *best_tile_cfg, float *best_ms);
 
 /*
+ * Mass h^d sum |Psi|^2 for callers that cannot allocate device memory.
+ * The paper has no counterpart; it exists for code that may not call
+ * cudaMalloc: work issued while another component captures the stream into
+ * a CUDA graph (allocation is illegal there), plug-ins whose host
+ * application owns all device memory through its own pool, and real-time
+ * loops that cannot take the device synchronisation an allocation may
+ * imply.  Such callers cannot create a context (it needs a workspace).
+ *   dims, N, h  the grid as in nlse_create (any N[k] >= 1)
+ *   dtype       NLSE_C128 / NLSE_C64_ACC64 (psi is double2) or NLSE_C64 (float2)
+ *   psi         device input;  out: device pointer to one double (the result)
+ *   stream      cudaStream_t as void* (NULL = legacy default stream)
+ * Asynchronous; the result is in *out once the stream reaches it.  The
+ * reduction's scratch (one pair of FP64 partial sums per block of 4096
+ * sites) is a fixed 128 KiB array inside the library that every GPU which
+ * loads the library keeps until the process exits, so grids above
+ * 8192 * 4096 = 33,554,432 sites are rejected with NLSE_EINVAL.  Nothing is
+ * allocated and no allocating library routine is called.  The first call on
+ * a device (with that device current) looks up the array's device address
+ * once; make that first call before any stream capture.  All calls share the
+ * array: calls whose kernels overlap on the GPU (several streams or host
+ * threads at once) race and must be serialised by the caller.  A NaN or Inf
+ * in psi yields a non-finite result (no status flag).  Errors: NLSE_EINVAL,
+ * NLSE_ECUDA, with the message in nlse_last_error().
+ */
+int nlse_mass_noalloc(int dims, const int64_t *N, double h, int dtype, const void *psi, double *out,
+                      void *stream);
+
+/*
  * Test hooks for the bounded device-side waits (not needed in normal use).
  *   NLSE_DEBUG_SPIN_LIMIT  value = SM clock cycles any device-side wait may
  *                          last before the kernel gives up (default ~2e9,

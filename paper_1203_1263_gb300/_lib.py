@@ -51,6 +51,7 @@ SIGNATURES = {
     "nlse_set_kernel": (_I, [_VP, _I, _I]),
     "nlse_debug_set": (_I, [_VP, _I, ctypes.c_longlong]),
     "nlse_autotune": (_I, [_VP, ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_float)]),
+    "nlse_mass_noalloc": (_I, [_I, _I64P, _D, _I, _VP, _VP, _VP]),
 }
 
 

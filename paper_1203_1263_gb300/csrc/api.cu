@@ -319,6 +319,9 @@ int read_status(nlse_ctx* c) {
 }  // namespace
 
 namespace nlse {
+// Lets other translation units of the library report through nlse_last_error().
+void record_last_error(const char* msg) { snprintf(g_err, sizeof(g_err), "%s", msg); }
+
 cudaError_t launch_round_master(const double2* master, float2* n32, int64_t total, cudaStream_t stream) {
   int64_t b = (total + 255) / 256;
   if (b > 152 * 16) b = 152 * 16;
