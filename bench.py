@@ -50,7 +50,17 @@ ALG_BYTES = {  # dtype -> (with V, without V)
     "c64": (152, 136),
     "c64_acc64": (176, 160),
 }
+# FP64 floating-point operations per site per RK4 step of the FP64 path (FMA = 2):
+# per stage |Psi|^2 (3), N = s|Psi|^2 - V (2), a*Lap = scale x exact integer
+# sum (2), F (4), and the stage update (stage 1: 4, stages 2 and 3: 8,
+# stage 4: 6).  The Laplacian's stencil sums run on the integer pipe.
+FP64_FLOPS_PER_SITE_STEP = 15 + 19 + 19 + 17
 CHUNK = 56   # steps per frame in the end-to-end measurement (the 87x87x203 run's chunk size)
+
+
+# DRAM bytes (read + write) per RK4 step of the stage kernels on this workload,
+# from one ncu capture (profiles/), or None when the kernels changed since.
+TRAFFIC_PER_STEP = {}
 
 
 def peaks():
@@ -59,6 +69,29 @@ def peaks():
         d = json.load(open(p))
         return float(d["hbm_gbs"]), "measured"
     return 6800.0, "fallback"
+
+
+# FP64 peak of a GB300: 152 SMs x 2 FP64 FMA lanes per cycle x 2 flops at the
+# 2070 MHz maximum clock = 1.26 TFLOP/s (the recipe's nominal 1.25); measured
+# with independent DFMA chains on the GB300s: 0.998 TFLOP/s.
+FP64_PEAK_TFLOPS_MEASURED = 0.998
+
+
+def roofline_for(dtype, sites, step_s, with_v):
+    """The roofline that binds each form: FP64 is bound by the FP64 pipe, the
+    FP32 forms by HBM."""
+    hbm_peak, kind = peaks()
+    bytes_site = ALG_BYTES[dtype][0 if with_v else 1]
+    gbs = sites * bytes_site / step_s / 1e9
+    hbm = {"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm_peak, "unit": "GB/s",
+           "frac": round(gbs / hbm_peak, 4), "peak_kind": kind, "alg_bytes_per_site_step": bytes_site}
+    if dtype != "c128":
+        return hbm, None
+    tflops = sites * FP64_FLOPS_PER_SITE_STEP / step_s / 1e12
+    alu = {"bound": "alu", "achieved": round(tflops, 4), "peak": FP64_PEAK_TFLOPS_MEASURED, "unit": "TFLOP/s",
+           "frac": round(tflops / FP64_PEAK_TFLOPS_MEASURED, 4), "peak_kind": "measured (FP64 FMA probe)",
+           "alg_flops_per_site_step": FP64_FLOPS_PER_SITE_STEP}
+    return alu, hbm
 
 
 # ---------------------------------------------------------------------------
@@ -142,7 +175,8 @@ def run_ours(args, rank, world, local_rank):
     def timed(dtype, K, Wm):
         with torch.cuda.stream(stream):
             g = Integrator(p.psi0, p.h, p.a, p.s, p.V, "msd", p.order, dtype, device=dev, stream=stream)
-            g.set_kernel(args.variant, args.tile)
+            if args.variant is not None or args.tile != -1:
+                g.set_kernel(args.variant if args.variant is not None else (2 if dtype == "c128" else 1), args.tile)
             g.step(Wm, dt)
             g.sync()
             barrier()
@@ -172,14 +206,10 @@ def run_ours(args, rank, world, local_rank):
 
     result = None
     if rank == 0:
-        hbm_peak, peak_kind = peaks()
-        bytes_site = ALG_BYTES[args.dtype][0 if p.V is not None else 1]
         step_s = ms_max * 1e-3 / K
-        achieved = sites * bytes_site / step_s / 1e9
-        roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_peak, "unit": "GB/s",
-                "frac": round(achieved / hbm_peak, 4), "traffic": None, "peak_kind": peak_kind,
-                "kernel": "k_stage (4 fused RK4 stages per step)",
-                "alg_bytes_per_site_step": bytes_site}
+        roof, hbm_view = roofline_for(args.dtype, sites, step_s, p.V is not None)
+        roof["traffic"] = TRAFFIC_PER_STEP.get(args.dtype)
+        roof["kernel"] = "one RK4 step: 4 fused stage kernels (deep interior, TMA-fed) + 4 wall-shell kernels"
         result = {
             "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world, "steps": K, "warmup": Wm,
             "ms_per_step": round(ms_max / K, 4), "higher_is_better": True, "scaling": "weak",
@@ -189,8 +219,10 @@ def run_ours(args, rank, world, local_rank):
                        "order": p.order, "bc": "msd", "dt": dt, "precision": args.dtype,
                        "l2": "inputs larger than L2 (%.0f MB per state array)" % (sites * 16 / 1e6),
                        "parallelism": "replicas" if world > 1 else "single"},
-            "roofline": roof, "clocks": clocks, "gpu_launches": 4 * K,
+            "roofline": roof, "clocks": clocks, "gpu_launches": 8 * K,
         }
+        if hbm_view is not None:
+            result["hbm_roofline"] = hbm_view
 
     # ---- other precision forms on the same problem (speed-up over FP64 at a stated accuracy) ----
     if not args.no_forms and rank == 0:
@@ -203,11 +235,10 @@ def run_ours(args, rank, world, local_rank):
             st = g2.numpy().astype(np.complex128)
             rl2 = float(np.linalg.norm((st - ref_state).ravel()) / np.linalg.norm(ref_state.ravel()))
             v2 = sites * K / (ms2 * 1e-3) / 1e9
-            b2 = ALG_BYTES[dt_name][0 if p.V is not None else 1]
-            ach = sites * b2 / (ms2 * 1e-3 / K) / 1e9
+            r2, _ = roofline_for(dt_name, sites, ms2 * 1e-3 / K, p.V is not None)
+            r2["traffic"] = TRAFFIC_PER_STEP.get(dt_name)
             forms[dt_name] = {"value": round(v2, 4), "unit": UNIT, "speedup_vs_f64": round(v2 / value, 3),
-                              "rel_l2_vs_f64_gpu": rl2, "hbm_gbs": round(ach, 1),
-                              "hbm_frac": round(ach / peaks()[0], 4)}
+                              "rel_l2_vs_f64_gpu": rl2, "roofline": r2}
             g2.close()
         result["forms"] = forms
 
@@ -220,7 +251,8 @@ def run_ours(args, rank, world, local_rank):
         frames = max(1, K // CHUNK)
         with torch.cuda.stream(stream):
             g = Integrator(p.psi0, p.h, p.a, p.s, p.V, "msd", p.order, args.dtype, device=dev, stream=stream)
-            g.set_kernel(args.variant, args.tile)
+            if args.variant is not None or args.tile != -1:
+                g.set_kernel(args.variant if args.variant is not None else (2 if args.dtype == "c128" else 1), args.tile)
             dev_psi = g.psi
             g.step(Wm, dt)
             g.sync()
@@ -323,7 +355,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="trap_vortex_3d_256x256x512")
     ap.add_argument("--dtype", choices=["c128", "c64", "c64_acc64"], default="c128")
-    ap.add_argument("--variant", type=int, default=1, help="stage kernel: 0 generic, 1 tiled")
+    ap.add_argument("--variant", type=int, default=None,
+                    help="stage kernel (default: the library's per-precision default)")
     ap.add_argument("--tile", type=int, default=-1, help="tiled kernel CTA shape (-1 default)")
     ap.add_argument("--no-forms", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")

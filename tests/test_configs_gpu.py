@@ -1,0 +1,132 @@
+"""The plain-method workloads end to end on the GPU, against the oracle and
+the exact solution.
+
+  bright soliton 1D   N = 2001, h = 0.05, dt = h^2/8, 32000 steps to t = 10, CD and 2SHOC
+  trap vortex 3D      87x87x203 (h = 0.2) and 256x256x512 (h = 17.2/255), 2SHOC, MSD,
+                      dt = 0.8 x the potential-aware stability bound
+  vortex rings 3D     512^3, h = 0.25, 2SHOC, MSD (the precision form's workload)
+
+Tolerances are the method's end-time bars: relative L2 <= 1e-12 (FP64) and
+<= 2e-5 (FP32 forms) against the FP64 oracle.  Full-size grids are checked
+over one step (the oracle runs the whole grid), smaller ones over more.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1203_1263_gb300 import workloads as W
+from paper_1203_1263_gb300.integrator import Integrator
+
+pytestmark = pytest.mark.gpu
+
+
+def rel_l2(a, b):
+    a = np.asarray(a, dtype=np.complex128)
+    return float(np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel()))
+
+
+def bound_dt(p):
+    s_rho = abs(p.s) * float(np.max(np.abs(p.psi0))) ** 2
+    return 0.8 * O.stability_bound(p.dims, p.h, p.a, p.order, p.vmax(), s_rho)
+
+
+@pytest.mark.parametrize("order", [2, 4])
+def test_bright_soliton_full_run(order):
+    """32000 RK4 steps to t = 10: FP64 matches the oracle to 1e-12 and the
+    exact soliton to the scheme's accuracy; the FP64-accumulator form stays
+    within 2e-5 of the oracle."""
+    p = W.bright_soliton_1d(order=order, n=2001, t_end=10.0)
+    ref, _ = O.run_problem(p)
+    exact = W.bright_soliton(p.extra["x"], p.extra["t_end"])
+    ref_err = rel_l2(ref, exact)          # the scheme's own error at t = 10
+    m0 = O.mass(p.psi0, p.h)
+    for dtype, tol, mtol in (("c128", 1e-12, 1e-9), ("c64_acc64", 2e-5, 1e-6)):
+        g = Integrator(p.psi0, p.h, p.a, p.s, None, "dirichlet", order, dtype)
+        g.step(p.steps, p.dt)
+        got = g.numpy()
+        assert rel_l2(got, ref) <= tol, (dtype, rel_l2(got, ref))
+        assert rel_l2(got, exact) <= ref_err + tol
+        assert abs(g.mass() - m0) <= mtol * m0
+
+
+@pytest.mark.parametrize("order", [2, 4])
+def test_bright_soliton_plain_fp32(order):
+    """Pure FP32 rounds the state every step; over the full 32000 steps its
+    error against the oracle is reported, and bounded by the FP32 bar over the
+    first 4000 steps."""
+    p = W.bright_soliton_1d(order=order, n=2001, t_end=10.0)
+    ref = O.rk4(p.psi0, p.h, p.a, p.s, p.dt, 4000, None, p.bc, order)
+    g = Integrator(p.psi0, p.h, p.a, p.s, None, "dirichlet", order, "c64")
+    g.step(4000, p.dt)
+    assert rel_l2(g.numpy(), ref) <= 2e-5
+
+
+@pytest.mark.parametrize("dtype,tol", [("c128", 1e-12), ("c64", 2e-5), ("c64_acc64", 2e-5)])
+def test_trap_vortex_87x87x203(dtype, tol):
+    p = W.trap_vortex_3d(shape=(203, 87, 87))
+    dt = bound_dt(p)
+    nsteps = 24
+    ref = O.rk4(p.psi0, p.h, p.a, p.s, dt, nsteps, p.V, p.bc, p.order)
+    g = Integrator(p.psi0, p.h, p.a, p.s, p.V, "msd", 4, dtype)
+    g.step(nsteps, dt)
+    got = g.numpy()
+    assert rel_l2(got, ref) <= tol
+    m_ref = O.mass(ref, p.h)
+    assert abs(g.mass() - m_ref) <= (1e-13 if dtype == "c128" else 2 * tol) * m_ref
+
+
+def test_trap_vortex_256x256x512_one_step_full_size():
+    """The benchmark's workload and launch configuration, one step, every site
+    against the oracle."""
+    p = W.trap_vortex_3d(shape=(512, 256, 256))
+    dt = bound_dt(p)
+    ref = O.rk4(p.psi0, p.h, p.a, p.s, dt, 1, p.V, p.bc, p.order)
+    for dtype, tol in (("c128", 1e-12), ("c64", 2e-5)):
+        g = Integrator(p.psi0, p.h, p.a, p.s, p.V, "msd", 4, dtype)
+        g.step(1, dt)
+        assert rel_l2(g.numpy(), ref) <= tol, dtype
+        g.close()
+
+
+def test_trap_vortex_long_run_fp32_forms_vs_fp64():
+    """3360 steps on 87x87x203 (the paper's headline step count): the FP32
+    forms against the FP64 GPU run.  Within the stability bound RK4 damps
+    (|R(iy)| <= 1), so the FP64 mass may only decrease; here it loses ~1e-3,
+    the stiff content of the non-smooth Thomas-Fermi edge."""
+    p = W.trap_vortex_3d(shape=(203, 87, 87))
+    dt = bound_dt(p)
+    runs = {}
+    for dtype in ("c128", "c64", "c64_acc64"):
+        g = Integrator(p.psi0, p.h, p.a, p.s, p.V, "msd", 4, dtype)
+        g.step(3360, dt)
+        runs[dtype] = (g.numpy(), g.mass())
+    ref, m = runs["c128"]
+    m0 = O.mass(p.psi0, p.h)
+    e_mix, e_32 = rel_l2(runs["c64_acc64"][0], ref), rel_l2(runs["c64"][0], ref)
+    print(f"3360 steps: mass drift {abs(m - m0) / m0:.3e}, rel-L2 vs FP64: c64_acc64 {e_mix:.3e}, c64 {e_32:.3e}")
+    assert m <= m0 * (1 + 1e-12)
+    assert abs(runs["c64_acc64"][1] - m) <= 1e-5 * m and abs(runs["c64"][1] - m) <= 1e-5 * m
+    assert e_mix <= 2e-5
+    assert e_32 <= 2e-5
+
+
+def test_vortex_rings_512cube_precision_form():
+    """512^3: one step of the FP64 and the FP32-with-FP64-accumulator forms
+    against the oracle on the full grid, then 100 steps of the two GPU forms
+    against each other (relative L2 and mass drift)."""
+    p = W.vortex_rings_3d(n=512)
+    dt = bound_dt(p)
+    ref = O.rk4(p.psi0, p.h, p.a, p.s, dt, 1, None, p.bc, p.order)
+    g64 = Integrator(p.psi0, p.h, p.a, p.s, None, "msd", 4, "c128")
+    gmx = Integrator(p.psi0, p.h, p.a, p.s, None, "msd", 4, "c64_acc64")
+    g64.step(1, dt)
+    gmx.step(1, dt)
+    assert rel_l2(g64.numpy(), ref) <= 1e-12
+    assert rel_l2(gmx.numpy(), ref) <= 2e-5
+    del ref
+    g64.step(99, dt)
+    gmx.step(99, dt)
+    a, b = g64.numpy(), gmx.numpy()
+    assert rel_l2(b, a) <= 2e-5
+    m64, mmx = g64.mass(), gmx.mass()
+    assert abs(mmx - m64) <= 1e-6 * m64
