@@ -248,13 +248,13 @@ def run_ours(args, rank, world, local_rank):
         host_np = p.psi0.astype(np.complex64) if args.dtype == "c64" else p.psi0
         host_in = torch.from_numpy(np.ascontiguousarray(host_np)).pin_memory()
         host_out = torch.empty_like(host_in).pin_memory()
-        frames = max(1, K // CHUNK)
+        frames = max(3, K // CHUNK)
         with torch.cuda.stream(stream):
             g = Integrator(p.psi0, p.h, p.a, p.s, p.V, "msd", p.order, args.dtype, device=dev, stream=stream)
             if args.variant is not None or args.tile != -1:
                 g.set_kernel(args.variant if args.variant is not None else (2 if args.dtype == "c128" else 1), args.tile)
             dev_psi = g.psi
-            g.step(Wm, dt)
+            g.step(CHUNK, dt)        # untimed frame: builds the step graph
             g.sync()
             barrier()
             w0 = time.perf_counter()

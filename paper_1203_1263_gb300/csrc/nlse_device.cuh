@@ -378,6 +378,36 @@ struct StageArgs {
   unsigned int* flag;          // bit 0: non-finite Psi
 };
 
+// float <-> double on the integer pipe (GB300 issues FP64-pipe instructions,
+// conversions included, at 1/75 of the FP32 rate).  Both follow IEEE-754:
+// widening is exact, narrowing rounds to nearest even; zeros, subnormals,
+// infinities and NaN take the hardware conversion.
+__device__ __forceinline__ double f2d_exact(float v) {
+  const unsigned int u = __float_as_uint(v);
+  const unsigned int e = (u >> 23) & 0xFFu;
+  if (e == 0u || e == 0xFFu) return double(v);
+  const unsigned long long bits = ((unsigned long long)(u & 0x80000000u) << 32) |
+                                  ((unsigned long long)(e - 127u + 1023u) << 52) |
+                                  ((unsigned long long)(u & 0x7FFFFFu) << 29);
+  return __longlong_as_double((long long)bits);
+}
+
+__device__ __forceinline__ float d2f_rn(double v) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(v);
+  const int e = int((u >> 52) & 0x7FF) - 1023 + 127;   // biased float exponent
+  if (e <= 0 || e >= 0xFF) return float(v);             // float subnormal/zero, overflow, Inf, NaN
+  const unsigned int sgn = (unsigned int)(u >> 32) & 0x80000000u;
+  const unsigned long long m = u & 0x000FFFFFFFFFFFFFull;
+  unsigned int mf = (unsigned int)(m >> 29);
+  const unsigned long long rem = m & 0x1FFFFFFFull, half = 0x10000000ull;
+  unsigned int ef = (unsigned int)e;
+  if (rem > half || (rem == half && (mf & 1u))) {
+    if (++mf == 0x800000u) { mf = 0; ++ef; }
+    if (ef >= 0xFFu) return float(v);                   // rounds up to overflow
+  }
+  return __uint_as_float(sgn | (ef << 23) | mf);
+}
+
 // The pointwise operands of one site's update, loaded ahead of use.
 template <class T>
 struct PointVals {
@@ -423,10 +453,11 @@ __device__ __forceinline__ void rk_apply(const StageArgs<T>& A, int64_t i, typen
       if constexpr (std::is_same<typename T::M, C>::value) {
         q.x = fma(A.dtc, p.K.x + F.x, p.mst.x);
         q.y = fma(A.dtc, p.K.y + F.y, p.mst.y);
-      } else {  // FP64 accumulator over FP32 stages
-        q.x = fma(A.dt6, double(p.K.x) + double(F.x), double(p.mst.x));
-        q.y = fma(A.dt6, double(p.K.y) + double(F.y), double(p.mst.y));
-        A.n32[i] = C{R(q.x), R(q.y)};
+      } else {  // FP64 accumulator over FP32 stages: the FP32 increment added to the FP64 master
+        const float ix = A.dtc * (p.K.x + F.x), iy = A.dtc * (p.K.y + F.y);
+        q.x = p.mst.x + f2d_exact(ix);
+        q.y = p.mst.y + f2d_exact(iy);
+        A.n32[i] = C{d2f_rn(q.x), d2f_rn(q.y)};
       }
       A.master[i] = q;
       if (!(isfinite(q.x) && isfinite(q.y))) atomicOr(A.flag, 1u);
