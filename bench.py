@@ -60,7 +60,10 @@ CHUNK = 56   # steps per frame in the end-to-end measurement (the 87x87x203 run'
 
 # DRAM bytes (read + write) per RK4 step of the stage kernels on this workload,
 # from one ncu capture (profiles/), or None when the kernels changed since.
-TRAFFIC_PER_STEP = {}
+TRAFFIC_PER_STEP = {  # one ncu capture of trap_vortex_3d_256x256x512, current kernels
+    "c128": 10712.0e6,
+    "c64": 5802.8e6,
+}
 
 
 def peaks():
@@ -208,7 +211,8 @@ def run_ours(args, rank, world, local_rank):
     if rank == 0:
         step_s = ms_max * 1e-3 / K
         roof, hbm_view = roofline_for(args.dtype, sites, step_s, p.V is not None)
-        roof["traffic"] = TRAFFIC_PER_STEP.get(args.dtype)
+        roof["traffic"] = TRAFFIC_PER_STEP.get(args.dtype) if args.workload == "trap_vortex_3d_256x256x512" else None
+        roof["traffic_unit"] = "bytes per RK4 step (ncu dram__bytes_read.sum + dram__bytes_write.sum)"
         roof["kernel"] = "one RK4 step: 4 fused stage kernels (deep interior, TMA-fed) + 4 wall-shell kernels"
         result = {
             "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world, "steps": K, "warmup": Wm,
@@ -236,7 +240,7 @@ def run_ours(args, rank, world, local_rank):
             rl2 = float(np.linalg.norm((st - ref_state).ravel()) / np.linalg.norm(ref_state.ravel()))
             v2 = sites * K / (ms2 * 1e-3) / 1e9
             r2, _ = roofline_for(dt_name, sites, ms2 * 1e-3 / K, p.V is not None)
-            r2["traffic"] = TRAFFIC_PER_STEP.get(dt_name)
+            r2["traffic"] = TRAFFIC_PER_STEP.get(dt_name) if args.workload == "trap_vortex_3d_256x256x512" else None
             forms[dt_name] = {"value": round(v2, 4), "unit": UNIT, "speedup_vs_f64": round(v2 / value, 3),
                               "rel_l2_vs_f64_gpu": rl2, "roofline": r2}
             g2.close()
