@@ -246,6 +246,9 @@ def run_ours(args, rank, world, local_rank):
             g2.close()
         result["forms"] = forms
 
+    if not args.no_batch and rank == 0:
+        result.setdefault("forms", {})["batch"] = batch_form(args, dev, min(K, 200), Wm)
+
     # ---- end to end through the public API: pinned host Psi in, CHUNK steps, Psi and mass out ----
     if not args.no_e2e:
         import torch
@@ -286,6 +289,60 @@ def run_ours(args, rank, world, local_rank):
         dist.barrier()
         dist.destroy_process_group()
     return result
+
+
+def batch_form(args, dev, K, Wm):
+    """512 independent uneven 2D runs (sides 64..1024, mixed a, s, V, order,
+    complex64) advanced together, against the plain FP64 GPU path (one
+    context per run, run one after another) and single-run FP32 contexts."""
+    import torch
+    from paper_1203_1263_gb300.integrator import BatchIntegrator, Integrator, max_dt
+    runs = []
+    for d in W.batch_runs_2d(nruns=args.batch_runs, seed=4):
+        p = W.batch_run_problem(d)
+        s_rho = abs(p.s) * float(np.max(np.abs(p.psi0))) ** 2
+        dt = 0.8 * max_dt(2, p.h, p.a, p.order, p.vmax(), s_rho)
+        runs.append(dict(psi0=p.psi0, h=p.h, a=p.a, s=p.s, dt=dt, V=p.V, bc="dirichlet", order=p.order))
+    sites = sum(r["psi0"].size for r in runs)
+    stream = torch.cuda.Stream(dev)
+
+    def timed(fn, steps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn(steps)
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1) * 1e-3
+
+    with torch.cuda.stream(stream):
+        b = BatchIntegrator(runs, device=dev, stream=stream)
+        tile, _ = b.autotune()
+        b.step(Wm)
+        b.sync()
+        t_batch = timed(b.step, K)
+        b.sync()
+        out = {}
+        for dtype in ("c128", "c64"):
+            gs = [Integrator(r["psi0"], r["h"], r["a"], r["s"], r["V"], "dirichlet", r["order"], dtype,
+                             device=dev, stream=stream) for r in runs]
+            for g, r in zip(gs, runs):
+                g.step(Wm, r["dt"])
+            torch.cuda.synchronize(dev)
+            t = timed(lambda n: [g.step(n, r["dt"]) for g, r in zip(gs, runs)], K)
+            out[dtype] = (t, gs)
+        ref = out["c128"][1]
+        errs = [float(np.linalg.norm(b.numpy(i).astype(np.complex128) - ref[i].numpy()) /
+                      np.linalg.norm(ref[i].numpy())) for i in range(len(runs))]
+    v_batch = sites * K / t_batch / 1e9
+    v64 = sites * K / out["c128"][0] / 1e9
+    v32 = sites * K / out["c64"][0] / 1e9
+    return {"value": round(v_batch, 4), "unit": UNIT, "runs": len(runs), "sites": int(sites), "steps": K,
+            "tile_cfg": tile, "speedup_vs_f64": round(v_batch / v64, 3),
+            "f64_sequential": round(v64, 4), "f32_sequential": round(v32, 4),
+            "speedup_vs_f32_sequential": round(v_batch / v32, 3),
+            "max_rel_l2_vs_f64_gpu": max(errs), "dtype": "f32",
+            "roofline": roofline_for("c64", sites, t_batch / K, True)[0]}
 
 
 def cpu_baseline(p, dt, budget_s=20.0, steps=None):
@@ -365,6 +422,8 @@ def main():
     ap.add_argument("--no-forms", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--batch-runs", type=int, default=512)
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--ref-budget", type=float, default=90.0)
     args = ap.parse_args()

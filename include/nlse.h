@@ -166,6 +166,50 @@ int nlse_set_kernel(nlse_t ctx, int variant, int tile_cfg);
  */
 int nlse_autotune(nlse_t ctx, int *best_tile_cfg, float *best_ms);
 
+/* ---------------------------------------------------------------------------
+ * Batched form: many independent 2D runs (uneven sizes and parameters) in
+ * complex64, advanced together with one launch per RK4 stage for all runs
+ * (a persistent deep-interior kernel over a (run, tile) work list and a
+ * wall-shell kernel over the runs' walls), the step loop replayed as a CUDA
+ * graph.  Each run is computed with the same per-site arithmetic as a
+ * single-run NLSE_C64 context with the tiled kernel, so its result is
+ * bit-for-bit that of integrating it alone.
+ * ------------------------------------------------------------------------- */
+typedef struct {
+  int64_t n[2];        /* (Ny, Nx), each >= 3 */
+  double h, a, s, dt;  /* spacing, dispersion, nonlinearity, this run's time step */
+  int bc, order;       /* NLSE_BC_*, 2 or 4 */
+  void *psi;           /* device complex64 (float2), caller-owned, advanced in place */
+  const void *V;       /* device float32 potential of the run's shape, or NULL */
+} nlse_run_desc;
+
+typedef struct nlse_batch *nlse_batch_t;
+
+/* Workspace bytes for the runs (per-run stage arrays, run table, work lists);
+ * 0 for invalid descriptors. */
+size_t nlse_batch_workspace_bytes(int nruns, const nlse_run_desc *runs);
+
+/* Create a batch over caller-owned device memory (descriptors are copied).
+ * Fails with NLSE_EUNSTABLE when a run's dt exceeds its RK4 linear bound
+ * (Sec. 3.4 with V = s = 0).  Synchronises the stream once (table upload). */
+int nlse_batch_create(nlse_batch_t *out, int nruns, const nlse_run_desc *runs, void *workspace, size_t ws_bytes,
+                      void *stream);
+
+/* Advance every run by nsteps RK4 steps of its own dt; asynchronous. */
+int nlse_batch_step(nlse_batch_t b, int64_t nsteps);
+
+/* Tile shape of the batched deep kernel (as nlse_set_kernel's tile_cfg; -1 = 64x8). */
+int nlse_batch_set_tile(nlse_batch_t b, int tile_cfg);
+
+/* Autotuner: time the tile shapes on the batch's own runs (stages 1-2 only,
+ * no run's Psi is written) and keep the fastest.  Synchronises the stream. */
+int nlse_batch_autotune(nlse_batch_t b, int *best_tile_cfg, float *best_ms);
+
+/* Wait for the stream; NLSE_ENONFINITE if any run produced a NaN or Inf. */
+int nlse_batch_sync(nlse_batch_t b);
+
+int nlse_batch_destroy(nlse_batch_t b);
+
 /*
  * Mass h^d sum |Psi|^2 for callers that cannot allocate device memory.
  * The paper has no counterpart; it exists for code that may not call

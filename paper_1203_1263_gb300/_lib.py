@@ -52,7 +52,21 @@ SIGNATURES = {
     "nlse_debug_set": (_I, [_VP, _I, ctypes.c_longlong]),
     "nlse_autotune": (_I, [_VP, ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_float)]),
     "nlse_mass_noalloc": (_I, [_I, _I64P, _D, _I, _VP, _VP, _VP]),
+    "nlse_batch_workspace_bytes": (ctypes.c_size_t, [_I, _VP]),
+    "nlse_batch_create": (_I, [ctypes.POINTER(_VP), _I, _VP, _VP, ctypes.c_size_t, _VP]),
+    "nlse_batch_step": (_I, [_VP, ctypes.c_int64]),
+    "nlse_batch_set_tile": (_I, [_VP, _I]),
+    "nlse_batch_autotune": (_I, [_VP, ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_float)]),
+    "nlse_batch_sync": (_I, [_VP]),
+    "nlse_batch_destroy": (_I, [_VP]),
 }
+
+
+class RunDesc(ctypes.Structure):
+    """nlse_run_desc of include/nlse.h."""
+    _fields_ = [("n", ctypes.c_int64 * 2), ("h", ctypes.c_double), ("a", ctypes.c_double), ("s", ctypes.c_double),
+                ("dt", ctypes.c_double), ("bc", ctypes.c_int), ("order", ctypes.c_int), ("psi", ctypes.c_void_p),
+                ("V", ctypes.c_void_p)]
 
 
 class NLSEError(RuntimeError):

@@ -138,3 +138,72 @@ class Integrator:
             self.close()
         except Exception:
             pass
+
+
+class BatchIntegrator:
+    """Many independent 2D runs (complex64) advanced together (nlse_batch_*).
+
+    runs: sequence of dicts with psi0 (complex array (Ny, Nx)), h, a, s, dt,
+    V (real array or None), bc ('dirichlet' | 'msd'), order (2 | 4)."""
+
+    def __init__(self, runs, device=None, stream=None):
+        self.lib = L.lib()
+        self.device = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+        self.psi = []
+        self.V = []
+        descs = (L.RunDesc * len(runs))()
+        for i, r in enumerate(runs):
+            p = torch.from_numpy(np.array(r["psi0"], dtype=np.complex64)).to(self.device).contiguous()
+            v = None if r.get("V") is None else \
+                torch.from_numpy(np.array(r["V"], dtype=np.float32)).to(self.device).contiguous()
+            self.psi.append(p)
+            self.V.append(v)
+            d = descs[i]
+            d.n[0], d.n[1] = p.shape
+            d.h, d.a, d.s, d.dt = float(r["h"]), float(r["a"]), float(r["s"]), float(r["dt"])
+            d.bc = _code(_BCS, r.get("bc", "dirichlet"))
+            d.order = int(r.get("order", 4))
+            d.psi = p.data_ptr()
+            d.V = None if v is None else v.data_ptr()
+        self._descs = descs
+        nbytes = int(self.lib.nlse_batch_workspace_bytes(len(runs), ctypes.byref(descs)))
+        if nbytes == 0:   # invalid descriptors: let create report the reason
+            b = ctypes.c_void_p()
+            L.check(self.lib.nlse_batch_create(ctypes.byref(b), len(runs), ctypes.byref(descs), None, 0, None))
+            raise L.NLSEError(L.NLSE_EINVAL, "invalid batch")
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        b = ctypes.c_void_p()
+        L.check(self.lib.nlse_batch_create(ctypes.byref(b), len(runs), ctypes.byref(descs),
+                                           self.workspace.data_ptr(), nbytes, self.stream.cuda_stream))
+        self.b = b
+
+    def step(self, nsteps: int) -> None:
+        L.check(self.lib.nlse_batch_step(self.b, int(nsteps)))
+
+    def sync(self) -> None:
+        L.check(self.lib.nlse_batch_sync(self.b))
+
+    def set_tile(self, tile_cfg: int) -> None:
+        L.check(self.lib.nlse_batch_set_tile(self.b, int(tile_cfg)))
+
+    def autotune(self):
+        cfg = ctypes.c_int()
+        ms = ctypes.c_float()
+        L.check(self.lib.nlse_batch_autotune(self.b, ctypes.byref(cfg), ctypes.byref(ms)))
+        return cfg.value, ms.value
+
+    def numpy(self, i: int) -> np.ndarray:
+        torch.cuda.current_stream(self.device).wait_stream(self.stream)
+        return self.psi[i].cpu().numpy()
+
+    def close(self) -> None:
+        if getattr(self, "b", None):
+            self.lib.nlse_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

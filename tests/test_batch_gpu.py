@@ -1,0 +1,90 @@
+"""Batched form: many uneven 2D runs advanced together.
+
+Each run in a batch is computed with the same per-site arithmetic as a
+single-run complex64 context using the tiled kernels, so the two must agree
+bit for bit; a sample of runs is also checked against the FP64 oracle
+(relative L2 <= 2e-5, the FP32 bar)."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1203_1263_gb300 import _lib as L
+from paper_1203_1263_gb300 import workloads as W
+from paper_1203_1263_gb300.integrator import BatchIntegrator, Integrator
+
+pytestmark = pytest.mark.gpu
+
+
+def small_runs(seed=4, nruns=14):
+    """Uneven runs with the batch workload's parameter recipe on smaller grids
+    (sides 5..150, including the degenerate 3 and 4)."""
+    runs = []
+    for i, d in enumerate(W.batch_runs_2d(nruns=nruns, seed=seed, nmin=5, nmax=150, h=0.25)):
+        if i == 0:
+            d["n"] = 3
+        if i == 1:
+            d["n"] = 4
+        p = W.batch_run_problem(d)
+        s_rho = abs(p.s) * float(np.max(np.abs(p.psi0))) ** 2
+        dt = 0.5 * O.stability_bound(2, p.h, p.a, p.order, p.vmax(), s_rho)
+        runs.append(dict(psi0=p.psi0, h=p.h, a=p.a, s=p.s, dt=dt, V=p.V, bc=["dirichlet", "msd"][i % 2],
+                         order=p.order))
+    return runs
+
+
+def test_batch_equals_single_runs_bitwise():
+    runs = small_runs()
+    b = BatchIntegrator(runs)
+    b.step(21)     # one graph replay of 16 steps + 5 single steps
+    b.sync()
+    for i, r in enumerate(runs):
+        g = Integrator(r["psi0"], r["h"], r["a"], r["s"], r["V"], r["bc"], r["order"], "c64")
+        g.set_kernel(1)
+        g.step(21, r["dt"])
+        assert np.array_equal(b.numpy(i), g.numpy()), i
+
+
+def test_batch_matches_oracle():
+    runs = small_runs(seed=9, nruns=8)
+    b = BatchIntegrator(runs)
+    b.step(12)
+    b.sync()
+    for i, r in enumerate(runs):
+        ref = O.rk4(r["psi0"], r["h"], r["a"], r["s"], r["dt"], 12, r["V"],
+                    W.BC_DIRICHLET if r["bc"] == "dirichlet" else W.BC_MSD, r["order"])
+        got = b.numpy(i).astype(np.complex128)
+        err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+        assert err <= 2e-5, (i, err)
+
+
+def test_batch_autotune_and_tiles_keep_results():
+    runs = small_runs(seed=5, nruns=10)
+    ref = BatchIntegrator(runs)
+    ref.step(6)
+    ref.sync()
+    b = BatchIntegrator(runs)
+    cfg, ms = b.autotune()
+    assert cfg in (0, 1, 2, 3) and ms > 0
+    b.step(6)
+    b.sync()
+    for t in (0, 1, 2):
+        c = BatchIntegrator(runs)
+        c.set_tile(t)
+        c.step(6)
+        c.sync()
+        for i in range(len(runs)):
+            assert np.array_equal(c.numpy(i), ref.numpy(i))
+    for i in range(len(runs)):
+        assert np.array_equal(b.numpy(i), ref.numpy(i))
+
+
+def test_batch_rejects_bad_runs():
+    runs = small_runs(nruns=3)
+    runs[2] = dict(runs[2], dt=runs[2]["dt"] * 1e3)
+    with pytest.raises(L.NLSEError) as e:
+        BatchIntegrator(runs)
+    assert e.value.code == L.NLSE_EUNSTABLE
+    runs = small_runs(nruns=3)
+    runs[1] = dict(runs[1], order=3)
+    with pytest.raises(L.NLSEError):
+        BatchIntegrator(runs)
