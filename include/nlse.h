@@ -210,6 +210,58 @@ int nlse_batch_sync(nlse_batch_t b);
 
 int nlse_batch_destroy(nlse_batch_t b);
 
+/* ---------------------------------------------------------------------------
+ * Learned surrogate (not in the paper): a residual 3x3-convolution network
+ * that maps a 2D complex64 state psi(t) to psi(t + window), trained on states
+ * the integrator itself produced.
+ *   h_{-1} = (Re psi, Im psi);  z_l = conv3x3_{dil_l}(h_{l-1}) + b_l,  h_l = silu(z_l)
+ *   (l = 0 .. layers-2, `channels` channels);  y = conv3x3(h_{layers-2}) + b (2 channels);
+ *   psi_out = psi_in + (y_0 + i y_1);  zero padding at the grid edges.
+ * Activations are channels-last; every convolution (forward, backward-data,
+ * weight-gradient) is an implicit GEMM on the tensor cores with BF16 operands
+ * and FP32 accumulation; parameters are FP32 masters (layout per layer: W
+ * [cout][9][cin] then b [cout]) with BF16 copies; loss = mean squared error of
+ * psi_out's real and imaginary parts; optimiser Adam (0.9, 0.999, 1e-8).
+ * All pointers are device pointers owned by the caller; states are float2
+ * arrays [nb][H][W].  Asynchronous unless a host output is requested.
+ * ------------------------------------------------------------------------- */
+typedef struct nlse_sur *nlse_sur_t;
+
+/* Number of FP32 parameters (0 for invalid shapes: channels 1..256, layers 2..16). */
+size_t nlse_sur_param_count(int channels, int layers);
+
+/* Workspace bytes for batches of up to max_batch states of H x W. */
+size_t nlse_sur_workspace_bytes(int H, int W, int channels, int layers, int max_batch);
+
+/* Create over caller-owned params (nlse_sur_param_count floats) and workspace. */
+int nlse_sur_create(nlse_sur_t *out, int H, int W, int channels, int layers, const int *dilations, int max_batch,
+                    float *params, void *workspace, size_t ws_bytes, void *stream);
+
+/* Seeded uniform initialisation of the parameters (SplitMix64), Adam state reset. */
+int nlse_sur_init(nlse_sur_t s, uint64_t seed);
+
+/* Refresh the BF16 copies after the caller wrote params directly. */
+int nlse_sur_sync_params(nlse_sur_t s);
+
+/* psi_out = network(psi_in) for nb states (nb <= max_batch).  With
+ * project_mass != 0 each output state is then rescaled by
+ * sqrt(M(psi_in) / M(psi_out)) (sums of |psi|^2 in FP64), so that it carries
+ * its input's mass, which the NLSE conserves; a state whose output mass is 0
+ * is left as it is.  psi_out must not overlap psi_in. */
+int nlse_sur_forward(nlse_sur_t s, int nb, const void *psi_in, void *psi_out, int project_mass);
+
+/* Loss gradient w.r.t. every parameter for (psi_in, psi_target) into grad_out
+ * (device, param layout; NULL to skip) and the loss into *loss_out (host;
+ * NULL to skip, else synchronises). */
+int nlse_sur_gradients(nlse_sur_t s, int nb, const void *psi_in, const void *psi_target, float *grad_out,
+                       double *loss_out);
+
+/* One Adam step on a batch (forward, backward, update); *loss_out as above. */
+int nlse_sur_train_step(nlse_sur_t s, int nb, const void *psi_in, const void *psi_target, float lr,
+                        double *loss_out);
+
+int nlse_sur_destroy(nlse_sur_t s);
+
 /*
  * Mass h^d sum |Psi|^2 for callers that cannot allocate device memory.
  * The paper has no counterpart; it exists for code that may not call

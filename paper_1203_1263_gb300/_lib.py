@@ -59,6 +59,16 @@ SIGNATURES = {
     "nlse_batch_autotune": (_I, [_VP, ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_float)]),
     "nlse_batch_sync": (_I, [_VP]),
     "nlse_batch_destroy": (_I, [_VP]),
+    "nlse_sur_param_count": (ctypes.c_size_t, [_I, _I]),
+    "nlse_sur_workspace_bytes": (ctypes.c_size_t, [_I, _I, _I, _I, _I]),
+    "nlse_sur_create": (_I, [ctypes.POINTER(_VP), _I, _I, _I, _I, ctypes.POINTER(_I), _I, _VP, _VP, ctypes.c_size_t,
+                             _VP]),
+    "nlse_sur_init": (_I, [_VP, ctypes.c_uint64]),
+    "nlse_sur_sync_params": (_I, [_VP]),
+    "nlse_sur_forward": (_I, [_VP, _I, _VP, _VP, _I]),
+    "nlse_sur_gradients": (_I, [_VP, _I, _VP, _VP, _VP, ctypes.POINTER(_D)]),
+    "nlse_sur_train_step": (_I, [_VP, _I, _VP, _VP, ctypes.c_float, ctypes.POINTER(_D)]),
+    "nlse_sur_destroy": (_I, [_VP]),
 }
 
 

@@ -1,0 +1,267 @@
+"""Learned surrogate for the 2D NLSE: one network call advances a state by a
+window of RK4 steps, re-checked against the plain RK4 path.
+
+Everything numeric runs in libnlse's kernels: the network's forward and
+backward passes and the Adam update (nlse_sur_*), the training data (the
+FP64 integrator), the mass checks (nlse_mass_noalloc) and the RK4 fallback.
+This module only orchestrates.
+"""
+from __future__ import annotations
+
+import ctypes
+import time
+from dataclasses import dataclass, field
+from typing import Optional
+
+import numpy as np
+import torch
+
+from . import _lib as L
+from . import workloads as W
+from .integrator import Integrator, max_dt
+
+
+class Surrogate:
+    """Residual 3x3-convolution network on (Re, Im) of an H x W state."""
+
+    def __init__(self, H: int, W_: int, channels: int = 64, layers: int = 6, dilations=(1, 2, 4, 8, 2, 1),
+                 max_batch: int = 16, device=None, stream=None, seed: int = 5):
+        self.lib = L.lib()
+        self.device = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+        self.H, self.W, self.C, self.L = H, W_, channels, layers
+        assert len(dilations) == layers
+        self.dilations = (ctypes.c_int * layers)(*dilations)
+        self.max_batch = max_batch
+        n = int(self.lib.nlse_sur_param_count(channels, layers))
+        if n == 0:
+            raise ValueError("bad surrogate shape")
+        self.params = torch.zeros(n, dtype=torch.float32, device=self.device)
+        nb = int(self.lib.nlse_sur_workspace_bytes(H, W_, channels, layers, max_batch))
+        self.workspace = torch.empty(nb, dtype=torch.uint8, device=self.device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        s = ctypes.c_void_p()
+        L.check(self.lib.nlse_sur_create(ctypes.byref(s), H, W_, channels, layers, self.dilations, max_batch,
+                                         self.params.data_ptr(), self.workspace.data_ptr(), nb,
+                                         self.stream.cuda_stream))
+        self.s = s
+        L.check(self.lib.nlse_sur_init(self.s, int(seed)))
+
+    @property
+    def nparams(self) -> int:
+        return self.params.numel()
+
+    def flops_per_state(self) -> float:
+        """Multiply-adds x 2 of one forward pass on one state."""
+        tot = 0
+        for l in range(self.L):
+            ci = 2 if l == 0 else self.C
+            co = 2 if l == self.L - 1 else self.C
+            tot += 2 * self.H * self.W * 9 * ci * co
+        return float(tot)
+
+    def load_params(self, values) -> None:
+        self.params.copy_(torch.as_tensor(values, dtype=torch.float32))
+        L.check(self.lib.nlse_sur_sync_params(self.s))
+
+    def forward(self, psi: torch.Tensor, project: bool = False, out: Optional[torch.Tensor] = None) -> torch.Tensor:
+        """Network output for [nb, H, W] states; project=True rescales each
+        output to its input's mass."""
+        psi = psi.to(self.device, torch.complex64).contiguous()
+        if out is None:
+            out = torch.empty_like(psi)
+        for i in range(0, psi.shape[0], self.max_batch):
+            j = min(i + self.max_batch, psi.shape[0])
+            L.check(self.lib.nlse_sur_forward(self.s, j - i, psi[i:j].data_ptr(), out[i:j].data_ptr(), int(project)))
+        return out
+
+    def _pair(self, psi: torch.Tensor, target: torch.Tensor):
+        psi = psi.to(self.device, torch.complex64).contiguous()
+        target = target.to(self.device, torch.complex64).contiguous()
+        if psi.shape != target.shape or tuple(psi.shape[1:]) != (self.H, self.W):
+            raise ValueError("psi and target must both be [nb, H, W]")
+        return psi, target
+
+    def gradients(self, psi: torch.Tensor, target: torch.Tensor):
+        """Gradient of the mean squared error w.r.t. the parameters, and the loss."""
+        psi, target = self._pair(psi, target)
+        grad = torch.empty_like(self.params)
+        loss = ctypes.c_double()
+        L.check(self.lib.nlse_sur_gradients(self.s, psi.shape[0], psi.data_ptr(), target.data_ptr(),
+                                             grad.data_ptr(), ctypes.byref(loss)))
+        return grad, loss.value
+
+    def train_step(self, psi: torch.Tensor, target: torch.Tensor, lr: float, want_loss: bool = True):
+        """One Adam step on the batch (psi, target); returns the loss before the step."""
+        psi, target = self._pair(psi, target)
+        loss = ctypes.c_double()
+        L.check(self.lib.nlse_sur_train_step(self.s, psi.shape[0], psi.data_ptr(), target.data_ptr(), float(lr),
+                                             ctypes.byref(loss) if want_loss else None))
+        return loss.value if want_loss else None
+
+    def close(self):
+        if getattr(self, "s", None):
+            self.lib.nlse_sur_destroy(self.s)
+            self.s = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---------------------------------------------------------------------------
+# training data from the FP64 integrator
+# ---------------------------------------------------------------------------
+FOCUSING = dict(a=1.0, s=1.0, h=0.2, dt=0.005, window=32)
+
+
+def generate_pairs(n_traj: int, windows: int, n: int = 256, seed: int = 5, device=None, params=FOCUSING,
+                   blowup: float = 10.0):
+    """(psi_t, psi_{t+window}) pairs, complex64 [N, n, n], from FP64 RK4 runs of
+    the focusing 2D NLSE with Dirichlet walls, 2SHOC.  Initial states: 1-4
+    Gaussian humps (workloads.humps_2d).  Trajectories whose max|psi| exceeds
+    `blowup` x its initial value (collapse) are dropped."""
+    dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+    X, Y = [], []
+    kept = 0
+    for k in range(n_traj):
+        psi0 = W.humps_2d(seed, k, n=n, h=params["h"])
+        g = Integrator(psi0, params["h"], params["a"], params["s"], None, "dirichlet", 4, "c128", device=dev)
+        amp0 = float(np.max(np.abs(psi0)))
+        states = [g.psi.to(torch.complex64).clone()]
+        ok = True
+        for _ in range(windows):
+            g.step(params["window"], params["dt"])
+            states.append(g.psi.to(torch.complex64).clone())
+        torch.cuda.synchronize(dev)
+        if float(states[-1].abs().max()) > blowup * amp0 or not torch.isfinite(torch.view_as_real(states[-1])).all():
+            ok = False
+        g.close()
+        if not ok:
+            continue
+        kept += 1
+        X.extend(states[:-1])
+        Y.extend(states[1:])
+    return torch.stack(X), torch.stack(Y), kept
+
+
+def train(sur: Surrogate, X: torch.Tensor, Y: torch.Tensor, epochs: int, batch: int, lr: float, seed: int = 0,
+          log_every: int = 0):
+    """Adam on shuffled mini-batches; returns the per-epoch mean loss."""
+    rng = np.random.default_rng(seed)
+    hist = []
+    for ep in range(epochs):
+        order = torch.from_numpy(rng.permutation(X.shape[0])).to(X.device)
+        tot, cnt = 0.0, 0
+        for i in range(0, X.shape[0] - batch + 1, batch):
+            idx = order[i:i + batch]
+            xb, yb = X[idx].contiguous(), Y[idx].contiguous()
+            loss = sur.train_step(xb, yb, lr, want_loss=(i // batch) % 8 == 0)
+            if loss is not None:
+                tot += loss
+                cnt += 1
+        hist.append(tot / max(cnt, 1))
+        if log_every and (ep + 1) % log_every == 0:
+            print(f"epoch {ep + 1}: loss {hist[-1]:.4e}")
+    return hist
+
+
+# ---------------------------------------------------------------------------
+# rollout with the RK4 re-check and fallback
+# ---------------------------------------------------------------------------
+@dataclass
+class RolloutStats:
+    windows: int = 0
+    accepted: int = 0          # windows taken from the network
+    rk4_windows: int = 0       # windows advanced by RK4 after a rejection (or by plain RK4)
+    rejected_l2: int = 0
+    rejected_mass: int = 0
+    checked: int = 0           # RK4 checks of a predicted window
+    seconds: float = 0.0
+    l2_errors: list = field(default_factory=list)
+    max_mass_drift: float = 0.0
+
+
+def _mass(psi: torch.Tensor, h: float, out: torch.Tensor) -> float:
+    lib = L.lib()
+    nn = L.int64_array(psi.shape)
+    L.check(lib.nlse_mass_noalloc(2, nn, float(h), L.C64, psi.data_ptr(), out.data_ptr(),
+                                  torch.cuda.current_stream(psi.device).cuda_stream))
+    return float(out.item())
+
+
+def rollout(sur: Optional[Surrogate], psi0, n_windows: int, params=FOCUSING, mode: str = "strict", every: int = 4,
+            tol_l2: float = 1e-2, tol_mass: float = 1e-4, project: bool = True, device=None):
+    """Advance psi0 by n_windows windows of `window` RK4 steps.
+
+    sur=None: plain FP64 RK4.  With a surrogate the rollout moves in spans of
+    one window ("strict") or `every` windows ("sampled").  Within a span each
+    window is predicted by the network from the previous prediction, and the
+    mass the network adds or removes over that window must stay within
+    tol_mass of the window's input mass (the NLSE conserves mass; what RK4
+    itself changes through its damping and the Dirichlet walls is not the
+    network's drift).  The span's last window is then re-run with FP64 RK4
+    from the same starting state and must agree within tol_l2 (relative L2).
+    If either check fails the rollout returns to the span's verified starting
+    state and advances the whole span with RK4.  States pass between windows
+    as complex64."""
+    if mode not in ("strict", "sampled"):
+        raise ValueError("mode must be 'strict' or 'sampled'")
+    dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+    h, dt, steps = params["h"], params["dt"], params["window"]
+    g = Integrator(np.asarray(psi0), h, params["a"], params["s"], None, "dirichlet", 4, "c128", device=dev)
+    st = RolloutStats()
+    mout = torch.zeros(1, dtype=torch.float64, device=dev)
+    verified = torch.as_tensor(np.asarray(psi0), dtype=torch.complex64, device=dev)[None].contiguous()
+    span_len = 1 if mode == "strict" else max(1, int(every))
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    if sur is None:
+        g.step(steps * n_windows, dt)
+        st.windows = st.rk4_windows = n_windows
+        verified = g.psi.to(torch.complex64)[None]
+    w = 0
+    while sur is not None and w < n_windows:
+        span = min(span_len, n_windows - w)
+        cur, cand, ok = verified, None, True
+        m_in = _mass(verified[0], h, mout)
+        for j in range(span):
+            if j:
+                cur = cand
+            cand = sur.forward(cur, project=project)
+            m_out = _mass(cand[0], h, mout)
+            drift = abs(m_out - m_in) / m_in
+            m_in = m_out
+            st.max_mass_drift = max(st.max_mass_drift, drift) if drift == drift else float("inf")
+            if not drift <= tol_mass:
+                ok = False
+                st.rejected_mass += 1
+                break
+        ref = None
+        if ok:
+            g.psi.copy_(cur[0].to(torch.complex128))
+            g.step(steps, dt)
+            ref = g.psi.to(torch.complex64)[None]
+            err = float(torch.linalg.vector_norm(cand - ref) / torch.linalg.vector_norm(ref))
+            st.checked += 1
+            st.l2_errors.append(err)
+            if err <= tol_l2:
+                st.accepted += span
+                verified = cand
+                w += span
+                continue
+            st.rejected_l2 += 1
+        if span == 1 and ref is not None:
+            verified = ref.contiguous()            # the check already advanced this window from `verified`
+        else:
+            g.psi.copy_(verified[0].to(torch.complex128))
+            g.step(steps * span, dt)
+            verified = g.psi.to(torch.complex64)[None].contiguous()
+        st.rk4_windows += span
+        w += span
+    st.windows = max(st.windows, w)
+    torch.cuda.synchronize(dev)
+    st.seconds = time.perf_counter() - t0
+    g.close()
+    return verified[0], st

@@ -1,0 +1,135 @@
+"""The surrogate's tensor-core kernels against the FP64 CPU reference, its
+training, its RK4 fallback, and what it gains over plain RK4."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import surrogate_ref as S
+from paper_1203_1263_gb300 import _lib as L_
+from paper_1203_1263_gb300 import workloads as W
+from paper_1203_1263_gb300.surrogate import FOCUSING, Surrogate, generate_pairs, rollout, train
+
+pytestmark = pytest.mark.gpu
+
+
+def bf16_round(a):
+    return torch.as_tensor(a).to(torch.bfloat16).to(torch.float64).numpy()
+
+
+def small_net(C=16, L=4, dil=(1, 2, 3, 1), H=24, Wd=28, nb=2, seed=11):
+    sur = Surrogate(H, Wd, channels=C, layers=L, dilations=dil, max_batch=nb, seed=seed)
+    z = W.random_field((nb, H, Wd), seed + 1)
+    psi = bf16_round(z.real) + 1j * bf16_round(z.imag)      # inputs exactly representable in BF16
+    target = psi * np.exp(0.3j) + 0.05
+    return sur, psi, target, C, L, dil
+
+
+# C = 16: every inner layer on the cp.async/ldmatrix kernels; C = 12: the generic kernel
+SHAPES = [dict(C=16, L=4, dil=(1, 2, 3, 1)), dict(C=12, L=3, dil=(2, 1, 1))]
+
+
+@pytest.mark.parametrize("shape", SHAPES, ids=["fast", "generic"])
+def test_forward_matches_reference(shape):
+    sur, psi, target, C, L, dil = small_net(**shape)
+    params = bf16_round(sur.params.cpu().numpy())
+    ref, _, _ = S.forward(params, psi, C, L, dil)
+    x = torch.as_tensor(psi, dtype=torch.complex64).cuda()
+    out = sur.forward(x).cpu().numpy()
+    dy_ref, dy = ref - psi, out - psi
+    assert np.linalg.norm(dy - dy_ref) <= 2e-2 * np.linalg.norm(dy_ref)
+    # mass projection: each state carries its input's mass
+    outp = sur.forward(x, project=True).cpu().numpy().astype(np.complex128)
+    refp = S.project_mass(psi, out.astype(np.complex128))
+    assert np.max(np.abs(outp - refp)) <= 1e-6 * np.max(np.abs(refp))
+    m_in = np.sum(np.abs(psi) ** 2, axis=(1, 2))
+    m_out = np.sum(np.abs(outp) ** 2, axis=(1, 2))
+    assert np.all(np.abs(m_out - m_in) <= 1e-6 * m_in)
+
+
+def test_forward_rejects_bad_batches():
+    sur, psi, target, C, L, dil = small_net()
+    x = torch.as_tensor(psi, dtype=torch.complex64).cuda()
+    with pytest.raises(L_.NLSEError) as e:
+        L_.check(sur.lib.nlse_sur_forward(sur.s, sur.max_batch + 1, x.data_ptr(), x.data_ptr(), 0))
+    assert e.value.code == L_.NLSE_EINVAL
+    with pytest.raises(ValueError):
+        sur.gradients(x, x[:1])
+
+
+@pytest.mark.parametrize("shape", SHAPES, ids=["fast", "generic"])
+def test_gradients_match_reference(shape):
+    """BF16 operands, FP32 accumulation: the gradient vector within 3 % (relative L2)."""
+    sur, psi, target, C, L, dil = small_net(**shape)
+    params = bf16_round(sur.params.cpu().numpy())
+    loss_ref, g_ref = S.loss_and_grad(params, psi, target, C, L, dil)
+    x = torch.as_tensor(psi, dtype=torch.complex64).cuda()
+    t = torch.as_tensor(target, dtype=torch.complex64).cuda()
+    g, loss = sur.gradients(x, t)
+    g = g.cpu().numpy().astype(np.float64)
+    assert abs(loss - loss_ref) <= 2e-2 * loss_ref
+    assert np.linalg.norm(g - g_ref) <= 3e-2 * np.linalg.norm(g_ref)
+    # every layer's weight block individually
+    off = 0
+    for co, ci in S.layer_shapes(C, L):
+        n = co * 9 * ci
+        blk, ref = g[off:off + n], g_ref[off:off + n]
+        assert np.linalg.norm(blk - ref) <= 5e-2 * np.linalg.norm(ref)
+        off += n + co
+
+
+def test_training_reduces_the_loss():
+    sur, psi, target, C, L, dil = small_net(nb=4, seed=21)
+    x = torch.as_tensor(psi, dtype=torch.complex64).cuda()
+    t = torch.as_tensor(target, dtype=torch.complex64).cuda()
+    first = sur.train_step(x, t, 3e-3)
+    for _ in range(300):
+        last = sur.train_step(x, t, 3e-3, want_loss=False)
+    last = sur.train_step(x, t, 3e-3)
+    assert last < 0.1 * first, (first, last)
+
+
+def test_fallback_takes_over_from_a_bad_network():
+    """A network that is far off (large random weights, no mass projection) is
+    rejected on every window, so the rollout equals plain RK4 (up to the
+    complex64 hand-over between windows)."""
+    n, windows = 48, 6
+    psi0 = W.humps_2d(5, 0, n=n, h=FOCUSING["h"])
+    sur = Surrogate(n, n, channels=16, layers=4, dilations=(1, 2, 2, 1), max_batch=1, seed=3)
+    sur.load_params(sur.params * 40.0)
+    ref, _ = rollout(None, psi0, windows)
+    for mode, project in (("strict", False), ("sampled", False), ("strict", True)):
+        got, st = rollout(sur, psi0, windows, mode=mode, every=3, project=project)
+        assert st.accepted == 0 and st.rk4_windows == windows
+        assert st.rejected_l2 + st.rejected_mass >= 1
+        if project:
+            assert st.rejected_l2 == windows and st.rejected_mass == 0
+        assert float(torch.linalg.vector_norm(got - ref) / torch.linalg.vector_norm(ref)) <= 1e-5
+
+
+def test_gain_over_plain_rk4():
+    """Train on FP64 RK4 windows of the focusing workload (64 x 64 grid here),
+    then roll out with the RK4 checks: every accepted window is within the
+    tolerance of RK4 from the same state, the final state stays close to the
+    plain RK4 rollout, and the wall-clock ratio is printed (on a grid this
+    small a window of RK4 is cheap, so the ratio may be below 1)."""
+    n, windows = 64, 20
+    X, Y, kept = generate_pairs(12, 10, n=n, seed=5)
+    sur = Surrogate(n, n, channels=32, layers=6, dilations=(1, 2, 4, 8, 2, 1), max_batch=16, seed=7)
+    hist = train(sur, X, Y, epochs=40, batch=16, lr=2e-3)
+    assert hist[-1] < 0.5 * hist[0]
+    psi0 = W.humps_2d(5, 100, n=n, h=FOCUSING["h"])
+    ref, st_plain = rollout(None, psi0, windows)
+    for mode in ("strict", "sampled"):
+        got, st = rollout(sur, psi0, windows, mode=mode, every=4)
+        err = float(torch.linalg.vector_norm(got - ref) / torch.linalg.vector_norm(ref))
+        print(f"\n{mode}: kept {kept} trajectories, loss {hist[0]:.3e} -> {hist[-1]:.3e}; accepted "
+              f"{st.accepted}/{st.windows}, rk4 {st.rk4_windows}, checked {st.checked}, rejected l2 "
+              f"{st.rejected_l2} mass {st.rejected_mass}; max check err {max(st.l2_errors, default=0):.3e}; "
+              f"final rel-L2 vs RK4 {err:.3e}; time plain {st_plain.seconds:.4f}s surrogate {st.seconds:.4f}s")
+        assert st.accepted + st.rk4_windows == windows
+        assert st.max_mass_drift <= 1e-6          # the mass projection holds each window's mass
+        accepted_errs = [e for e in st.l2_errors if e <= 1e-2]
+        assert len(accepted_errs) >= st.accepted // (1 if mode == "strict" else 4)
+        assert err <= windows * 1e-2 + 1e-5
