@@ -74,6 +74,14 @@ def peaks():
     return 6800.0, "fallback"
 
 
+def bf16_peak():
+    """Dense bf16 tensor peak (TFLOP/s, burst) and where it came from."""
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        return float(json.load(open(p))["bf16_tflops"]), "measured bf16 burst (cuBLAS)"
+    return 1900.0, "fallback bf16 burst"
+
+
 # FP64 peak of a GB300: 152 SMs x 2 FP64 FMA lanes per cycle x 2 flops at the
 # 2070 MHz maximum clock = 1.26 TFLOP/s (the recipe's nominal 1.25); measured
 # with independent DFMA chains on this pool's GB300s: 0.998 TFLOP/s.
@@ -249,6 +257,9 @@ def run_ours(args, rank, world, local_rank):
     if not args.no_batch and rank == 0:
         result.setdefault("forms", {})["batch"] = batch_form(args, dev, min(K, 200), Wm)
 
+    if not args.no_surrogate and rank == 0:
+        result.setdefault("forms", {})["surrogate"] = surrogate_form(args, dev)
+
     # ---- end to end through the public API: pinned host Psi in, CHUNK steps, Psi and mass out ----
     if not args.no_e2e:
         import torch
@@ -408,6 +419,101 @@ def run_reference(args, rank, world):
             "e2e": {"value": round(v, 6), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+def surrogate_form(args, dev):
+    """Learned surrogate on the 2D focusing workload (256 x 256, h = 0.2, one
+    window = 32 RK4 steps of dt = 0.005): tensor-core throughput of training
+    and inference, then a budgeted training run on FP64-integrator pairs and
+    RK4-checked rollouts to t = 20 (125 windows) against plain FP64 RK4."""
+    import torch
+    from paper_1203_1263_gb300.integrator import Integrator
+    from paper_1203_1263_gb300.surrogate import FOCUSING, Surrogate, generate_pairs, rollout, train
+    n, C, nl, dil, nb = 256, 64, 6, (1, 2, 4, 8, 4, 1), 16
+    h, dt, win = FOCUSING["h"], FOCUSING["dt"], FOCUSING["window"]
+    stream = torch.cuda.current_stream(dev)
+    out = {"grid": [n, n], "channels": C, "layers": nl, "dilations": list(dil), "batch": nb,
+           "window_steps": win, "dt": dt, "dtype": "bf16 operands, f32 accumulate"}
+
+    def ev_time(fn, reps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1) * 1e-3 / reps
+
+    # ---- kernel throughput on seeded states (a separate instance: these steps move its weights) ----
+    probe = Surrogate(n, n, channels=C, layers=nl, dilations=dil, max_batch=nb, seed=3)
+    x = torch.as_tensor(np.stack([W.humps_2d(11, i, n=n, h=h) for i in range(nb)]), dtype=torch.complex64,
+                        device=dev)
+    y = x * np.exp(0.1j)
+    for _ in range(3):
+        probe.train_step(x, y, 1e-4, want_loss=False)
+    t_train = ev_time(lambda: probe.train_step(x, y, 1e-4, want_loss=False), 20)
+    t_fwd = ev_time(lambda: probe.forward(x, project=True), 20)
+    x1 = x[:1].contiguous()
+    t_fwd1 = ev_time(lambda: probe.forward(x1, project=True), 20)
+    probe.close()
+    peak_tf, peak_kind = bf16_peak()
+    train_tf = probe.train_flops_per_state() * nb / t_train / 1e12
+    fwd_tf = probe.flops_per_state() * nb / t_fwd / 1e12
+    out["train_tflops"] = round(train_tf, 2)
+    out["train_states_per_s"] = round(nb / t_train, 1)
+    out["infer_tflops"] = round(fwd_tf, 2)
+    out["infer_ms_per_window_batch16"] = round(t_fwd / nb * 1e3, 4)
+    out["infer_ms_per_window_single"] = round(t_fwd1 * 1e3, 4)
+    out["roofline"] = {"bound": "tensor", "achieved": round(train_tf, 2), "peak": peak_tf, "unit": "TFLOP/s",
+                       "frac": round(train_tf / peak_tf, 4) if peak_tf else None, "traffic": None,
+                       "kernel": "one training step (forward, backward-data, weight-gradient convolutions)",
+                       "peak_kind": peak_kind}
+    # ---- one window of plain RK4 on one 256 x 256 state ----
+    psi_probe = W.humps_2d(11, 0, n=n, h=h)
+    for dtype in ("c128", "c64"):
+        g = Integrator(psi_probe, h, FOCUSING["a"], FOCUSING["s"], None, "dirichlet", 4, dtype, device=dev)
+        g.step(win, dt)
+        torch.cuda.synchronize(dev)
+        out[f"rk4_ms_per_window_{dtype}"] = round(ev_time(lambda: g.step(win, dt), 10) * 1e3, 4)
+        g.close()
+    # ---- budgeted training on FP64-integrator pairs, then rollouts ----
+    t0 = time.perf_counter()
+    X, Y, kept = generate_pairs(args.sur_traj, 125, n=n, seed=5, device=dev)
+    t_gen = time.perf_counter() - t0
+    sur = Surrogate(n, n, channels=C, layers=nl, dilations=dil, max_batch=nb, seed=7)
+    t0 = time.perf_counter()
+    hist = train(sur, X, Y, epochs=args.sur_epochs, batch=nb, lr=1e-3, lr_end=2e-5, seed=0)
+    torch.cuda.synchronize(dev)
+    t_train_run = time.perf_counter() - t0
+    del X, Y
+    psi0 = None
+    for j in range(8):          # a held-out initial state whose trajectory does not collapse
+        Xh, _, k = generate_pairs(1, 125, n=n, seed=99 + j, device=dev)
+        if k:
+            psi0 = Xh[0].cpu().numpy().astype(np.complex128)
+            break
+    out["training"] = {"pairs": int(kept * 125), "trajectories": kept, "epochs": args.sur_epochs,
+                       "loss_first_epoch": hist[0], "loss_last_epoch": hist[-1],
+                       "data_seconds": round(t_gen, 2), "train_seconds": round(t_train_run, 2)}
+    rollout(None, psi0, 2)                       # first calls load the kernels of the checks
+    rollout(sur, psi0, 2, mode="strict")
+    ref, st_plain = rollout(None, psi0, 125)
+    rolls = {"plain_f64_seconds": round(st_plain.seconds, 4)}
+    for mode in ("strict", "sampled"):
+        got, st = rollout(sur, psi0, 125, mode=mode, every=4)
+        err = float(torch.linalg.vector_norm(got - ref) / torch.linalg.vector_norm(ref))
+        rolls[mode] = {"seconds": round(st.seconds, 4), "speedup_vs_f64": round(st_plain.seconds / st.seconds, 3),
+                       "accepted_windows": st.accepted, "rk4_windows": st.rk4_windows, "checked": st.checked,
+                       "rejected_l2": st.rejected_l2, "rejected_mass": st.rejected_mass,
+                       "max_mass_drift_per_window": st.max_mass_drift,
+                       "median_check_rel_l2": float(np.median(st.l2_errors)) if st.l2_errors else None,
+                       "final_rel_l2_vs_plain_f64": err}
+    rolls["every"] = 4
+    rolls["tolerances"] = {"rel_l2": 1e-2, "mass_drift": 1e-4}
+    out["rollout_t20"] = rolls
+    sur.close()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -424,6 +530,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--batch-runs", type=int, default=512)
+    ap.add_argument("--no-surrogate", action="store_true")
+    ap.add_argument("--sur-traj", type=int, default=48, help="surrogate training trajectories (125 windows each)")
+    ap.add_argument("--sur-epochs", type=int, default=10)
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--ref-budget", type=float, default=90.0)
     args = ap.parse_args()

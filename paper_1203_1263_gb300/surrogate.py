@@ -9,6 +9,7 @@ This module only orchestrates.
 from __future__ import annotations
 
 import ctypes
+import math
 import time
 from dataclasses import dataclass, field
 from typing import Optional
@@ -50,14 +51,22 @@ class Surrogate:
     def nparams(self) -> int:
         return self.params.numel()
 
-    def flops_per_state(self) -> float:
-        """Multiply-adds x 2 of one forward pass on one state."""
-        tot = 0
+    def _layer_flops(self):
+        out = []
         for l in range(self.L):
             ci = 2 if l == 0 else self.C
             co = 2 if l == self.L - 1 else self.C
-            tot += 2 * self.H * self.W * 9 * ci * co
-        return float(tot)
+            out.append(2.0 * self.H * self.W * 9 * ci * co)
+        return out
+
+    def flops_per_state(self) -> float:
+        """Multiply-adds x 2 of one forward pass on one state."""
+        return float(sum(self._layer_flops()))
+
+    def train_flops_per_state(self) -> float:
+        """Forward + weight-gradient of every layer + backward-data of layers 1.. (x 2 flops per multiply-add)."""
+        f = self._layer_flops()
+        return float(3 * sum(f) - f[0])
 
     def load_params(self, values) -> None:
         self.params.copy_(torch.as_tensor(values, dtype=torch.float32))
@@ -147,17 +156,23 @@ def generate_pairs(n_traj: int, windows: int, n: int = 256, seed: int = 5, devic
 
 
 def train(sur: Surrogate, X: torch.Tensor, Y: torch.Tensor, epochs: int, batch: int, lr: float, seed: int = 0,
-          log_every: int = 0):
-    """Adam on shuffled mini-batches; returns the per-epoch mean loss."""
+          log_every: int = 0, lr_end: Optional[float] = None):
+    """Adam on shuffled mini-batches; returns the per-epoch mean loss.  With
+    lr_end the rate follows a cosine from lr down to lr_end over the run."""
     rng = np.random.default_rng(seed)
     hist = []
+    per_epoch = max(1, X.shape[0] // batch)
+    total = epochs * per_epoch
+    it = 0
     for ep in range(epochs):
         order = torch.from_numpy(rng.permutation(X.shape[0])).to(X.device)
         tot, cnt = 0.0, 0
         for i in range(0, X.shape[0] - batch + 1, batch):
             idx = order[i:i + batch]
             xb, yb = X[idx].contiguous(), Y[idx].contiguous()
-            loss = sur.train_step(xb, yb, lr, want_loss=(i // batch) % 8 == 0)
+            rate = lr if lr_end is None else lr_end + 0.5 * (lr - lr_end) * (1 + math.cos(math.pi * it / total))
+            it += 1
+            loss = sur.train_step(xb, yb, rate, want_loss=(i // batch) % 8 == 0)
             if loss is not None:
                 tot += loss
                 cnt += 1
