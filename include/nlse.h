@@ -260,6 +260,20 @@ int nlse_sur_gradients(nlse_sur_t s, int nb, const void *psi_in, const void *psi
 int nlse_sur_train_step(nlse_sur_t s, int nb, const void *psi_in, const void *psi_target, float lr,
                         double *loss_out);
 
+/* Convolution kernels: 1 (default) runs the forward and backward-data
+ * convolutions of layers whose gathered and output channel counts are
+ * multiples of 16 (output channels 16..256, dilation <= 16) on the tcgen05
+ * tensor-core kernel (TMEM accumulators); 0 keeps every convolution on the
+ * mma.sync kernels.  Both give the same results up to FP32 summation order.
+ * NLSE_EINVAL for other values. */
+int nlse_sur_set_kernel(nlse_sur_t s, int tensor_core_gen);
+
+/* Wait for the stream.  NLSE_ETIMEOUT if a bounded wait inside a tcgen05
+ * kernel ran out since the last check (the kernel then stopped early and its
+ * outputs are incomplete); gradients / train_step report the same when they
+ * return a loss. */
+int nlse_sur_sync(nlse_sur_t s);
+
 int nlse_sur_destroy(nlse_sur_t s);
 
 /*

@@ -322,6 +322,9 @@ namespace nlse {
 // Lets other translation units of the library report through nlse_last_error().
 void record_last_error(const char* msg) { snprintf(g_err, sizeof(g_err), "%s", msg); }
 
+// cuTensorMapEncodeTiled for other translation units (nullptr when unavailable).
+void* tensor_map_encoder() { return reinterpret_cast<void*>(encode_fn()); }
+
 cudaError_t launch_round_master(const double2* master, float2* n32, int64_t total, cudaStream_t stream) {
   int64_t b = (total + 255) / 256;
   if (b > 152 * 16) b = 152 * 16;

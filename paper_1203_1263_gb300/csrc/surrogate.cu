@@ -17,6 +17,7 @@
 //   weight-grad    M = Cout,   N = 9 Cin, K = pixels: A[co,p] = dz[p, co], B[p,(t,ci)] = h[p + d o_t, ci]
 // Loss: mean squared error of psi_out against the target (Re and Im parts);
 // optimiser: Adam.
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <math.h>
@@ -29,6 +30,7 @@
 
 namespace nlse {
 void record_last_error(const char* msg);
+void* tensor_map_encoder();
 }
 
 namespace {
@@ -83,9 +85,10 @@ struct ConvArgs {
   const bf16* dz;       // backward: gradient w.r.t. the layer's pre-activation (Cout channels)
   const bf16* w;        // BF16 weights [Cout][9][Cin]
   const float* bias;    // forward
-  float* z;             // forward: pre-activation out (FP32), or the raw output of the last layer
+  float* z;             // forward: the last layer's output y (FP32), else nullptr
   bf16* h;              // forward: silu(z) out (BF16); nullptr for the last layer
-  const float* zprev;   // backward-data: pre-activation of the previous layer (for silu'), nullptr = none
+  bf16* sd;             // forward (training): silu'(z) out (BF16), else nullptr
+  const bf16* sdprev;   // backward-data: silu'(z) of the layer below (BF16), nullptr = none
   bf16* dzprev;         // backward-data: gradient w.r.t. the previous layer's pre-activation (BF16)
   float* dw;            // weight-grad: FP32 accumulation [Cout][9][Cin]
   int64_t kchunk;       // weight-grad: pixels per CTA
@@ -201,10 +204,11 @@ __global__ void __launch_bounds__(kThreads) k_conv(const ConvArgs a) {
         const float v = acc[i][j][r];
         if (MODE == MODE_FWD) {
           const float zv = v + a.bias[n];
-          a.z[m * a.cout + n] = zv;
+          if (a.z) a.z[m * a.cout + n] = zv;
+          if (a.sd) a.sd[m * a.cout + n] = __float2bfloat16_rn(dsilu(zv));
           if (a.h) a.h[m * a.cout + n] = __float2bfloat16_rn(silu(zv));
         } else if (MODE == MODE_BWD_DATA) {
-          const float d = a.zprev ? v * dsilu(a.zprev[m * a.cin + n]) : v;
+          const float d = a.sdprev ? v * __bfloat162float(a.sdprev[m * a.cin + n]) : v;
           a.dzprev[m * a.cin + n] = __float2bfloat16_rn(d);
         } else {
           atomicAdd(&a.dw[m * (9 * a.cin) + n], v);   // dw[co][t][ci], n = t * Cin + ci
@@ -443,25 +447,28 @@ __global__ void __launch_bounds__(WM * WN * 32) k_conv_fast(const ConvArgs a, co
         if (MODE == MODE_FWD) {
           if (n + 1 < N) {
             const float z0 = v0 + a.bias[n], z1 = v1 + a.bias[n + 1];
-            *reinterpret_cast<float2*>(&a.z[m * a.cout + n]) = make_float2(z0, z1);
+            if (a.z) *reinterpret_cast<float2*>(&a.z[m * a.cout + n]) = make_float2(z0, z1);
+            if (a.sd)
+              *reinterpret_cast<__nv_bfloat162*>(&a.sd[m * a.cout + n]) = __floats2bfloat162_rn(dsilu(z0), dsilu(z1));
             if (a.h)
               *reinterpret_cast<__nv_bfloat162*>(&a.h[m * a.cout + n]) = __floats2bfloat162_rn(silu(z0), silu(z1));
           } else if (n < N) {
             const float z0 = v0 + a.bias[n];
-            a.z[m * a.cout + n] = z0;
+            if (a.z) a.z[m * a.cout + n] = z0;
+            if (a.sd) a.sd[m * a.cout + n] = __float2bfloat16_rn(dsilu(z0));
             if (a.h) a.h[m * a.cout + n] = __float2bfloat16_rn(silu(z0));
           }
         } else if (MODE == MODE_BWD_DATA) {
           if (n + 1 < N) {
             float d0 = v0, d1 = v1;
-            if (a.zprev) {
-              const float2 zp = *reinterpret_cast<const float2*>(&a.zprev[m * a.cin + n]);
-              d0 *= dsilu(zp.x);
-              d1 *= dsilu(zp.y);
+            if (a.sdprev) {
+              const float2 sp = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&a.sdprev[m * a.cin + n]));
+              d0 *= sp.x;
+              d1 *= sp.y;
             }
             *reinterpret_cast<__nv_bfloat162*>(&a.dzprev[m * a.cin + n]) = __floats2bfloat162_rn(d0, d1);
           } else if (n < N) {
-            const float d0 = a.zprev ? v0 * dsilu(a.zprev[m * a.cin + n]) : v0;
+            const float d0 = a.sdprev ? v0 * __bfloat162float(a.sdprev[m * a.cin + n]) : v0;
             a.dzprev[m * a.cin + n] = __float2bfloat16_rn(d0);
           }
         } else {
@@ -469,6 +476,572 @@ __global__ void __launch_bounds__(WM * WN * 32) k_conv_fast(const ConvArgs a, co
           if (n + 1 < N) atomicAdd(&a.dw[m * N + n + 1], v1);
         }
       }
+}
+
+// ---------------------------------------------------------------------------
+// Tensor-core (tcgen05) convolution for forward and backward-data passes.
+//
+// One tile = 128 consecutive pixels of one image row (M = 128), all output
+// channels (N = nout <= 256).  The CTA copies the tile's halo once: image rows
+// y - d, y, y + d and columns x0 - d .. x0 + 127 + d, every gathered channel,
+// zero outside the image, into shared memory in the no-swizzle K-major
+// core-matrix layout
+//     byte (kc * 3 * RW + r * RW + c) * 16 + 2 * (ci % 8),  kc = ci / 8, RW = 128 + 2d,
+// i.e. the 16-byte channel chunk of halo pixel (r, c) in plane kc.  Pixels
+// sit 16 bytes apart inside a plane, so the A operand of tap (dy, dx) is the
+// same buffer with the descriptor's start moved by ((1 + sy) RW + d + sx d) * 16
+// bytes ((sy, sx) = (dy, dx) forward, -(dy, dx) backward): nine taps, one
+// copy.  The weights of all nine taps stay in shared memory for the whole
+// persistent CTA in the same layout (rows = output channels).  One thread
+// issues the 9 x (K / 16) tcgen05.mma.kind::f16 per tile into a TMEM
+// accumulator (double-buffered: 2 x nout FP32 columns), tcgen05.commit
+// signals an mbarrier, and the eight warps read the previous tile's
+// accumulator with tcgen05.ld for the fused epilogue while the tensor core
+// works on the current one.  Halo copies use cp.async (zero-fill) one tile
+// ahead.  Every mbarrier wait is bounded; a wait that runs out sets *err,
+// and the CTA stops, frees its TMEM and returns.
+// ---------------------------------------------------------------------------
+struct TcArgs {
+  Geo g;
+  int cg;              // gathered channels = K per tap (multiple of 16)
+  int nout;            // output channels = N (multiple of 16, <= 256)
+  int dil;
+  const bf16* act;     // gathered activation, channels-last [P][cg]
+  const bf16* wsrc;    // forward: W[nout][9][cg]; backward: WT[9][nout][cg]
+  const float* bias;   // forward
+  float* z;            // forward: the last layer's output [P][nout] (FP32), else nullptr
+  bf16* h;             // forward: silu(z) (BF16), or nullptr
+  bf16* sd;            // forward (training): silu'(z) (BF16), or nullptr
+  const bf16* sdprev;  // backward: silu'(z) of the layer below [P][nout] (BF16), or nullptr
+  bf16* dzprev;        // backward: output gradient [P][nout] (BF16)
+  int* err;            // set to 1 when a wait runs out
+  long long spin_limit;
+};
+
+__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(b)), "r"(count));
+}
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, long long limit) {
+  const uint32_t addr = smem_u32(b);
+  for (long long it = 0; it < limit; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(addr), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+
+// shared-memory matrix descriptor: no swizzle, K-major, LBO = byte distance of
+// K-adjacent core matrices, SBO = byte distance of M/N-adjacent core matrices
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFF);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+  d |= (uint64_t)1 << 46;          // descriptor version for tcgen05
+  return d;                        // base offset 0, layout type 0 (no swizzle)
+}
+// instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both K-major, M x N
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+__device__ __forceinline__ void tc_mma(uint32_t dtmem, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
+      "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+}
+__device__ __forceinline__ void tc_commit(uint64_t* b) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(smem_u32(b))
+               : "memory");
+}
+__device__ __forceinline__ void tc_ld8(uint32_t taddr, float v[8]) {
+  uint32_t r[8];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Roles: warps 0-1 copy halos (cp.async, two tiles in flight, each thread
+// waits for its own copies, fences them into the async proxy and arrives on
+// the stage's "full" barrier); warp 2 (one lane) issues the MMAs of a tile
+// once its halo is full and its accumulator empty, and commits to the
+// stage's "empty" and the accumulator's "full" barriers; warps 3-10 drain an
+// accumulator (warp w reads TMEM lane quarter w % 4 and half of the columns),
+// release it and finish the epilogue.  Tile i uses halo stage and accumulator
+// i & 1.
+constexpr int kTcThreads = 352, kTcProducers = 64, kTcEpiWarps = 8;
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
+  asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(smem_u32(b)) : "memory");
+}
+__device__ __forceinline__ void tc_ld32(uint32_t taddr, float v[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// bounded wait that also gives up once another role has aborted
+__device__ __forceinline__ bool role_wait(uint64_t* b, uint32_t parity, long long limit, volatile int* abort_flag) {
+  for (long long it = 0; it < limit; it += 64) {
+    if (mbar_wait(b, parity, 64)) return true;
+    if (*abort_flag) return false;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(b)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* tm, int c0, int c1, int c2, int c3,
+                                            uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+      "[%6];\n" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(tm)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
+      : "memory");
+}
+// 128-byte-swizzled descriptor (8-row atoms of 1024 bytes).  The swizzle
+// phase follows the absolute shared-memory address (as TMA writes it), so a
+// start moved by whole 128-byte rows inside an atom needs no base offset.
+// lbo: K-major - unused inside one atom; MN-major - byte distance of the two
+// 64-element halves of a 128-wide operand.
+__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr, uint32_t lbo = 16) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFF);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+  d |= (uint64_t)(1024 >> 4) << 32;             // stride byte offset: next 8 rows
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;                       // SWIZZLE_128B
+  return d;
+}
+
+// LAYOUT 0: no-swizzle core-matrix halo filled by cp.async (any cg that is a
+// multiple of 16).  LAYOUT 1: cg = 64, halo rows of 128 bytes per pixel in the
+// 128-byte-swizzled layout, filled by three TMA copies per tile (zero fill
+// outside the image), weights stored in the same layout.
+template <int MODE, int LAYOUT>
+__global__ void __launch_bounds__(kTcThreads, 1) k_conv_tc(const TcArgs a, const __grid_constant__ CUtensorMap tmap) {
+  extern __shared__ __align__(1024) uint8_t tc_smem_raw[];
+  __shared__ __align__(8) uint64_t full_b[2], empty_b[2], accf_b[2], acce_b[2];
+  __shared__ uint32_t tmem_slot;
+  __shared__ float sbias[256];
+  __shared__ volatile int abort_flag;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const Geo& g = a.g;
+  // 1024-aligned base (the swizzled layouts need it; the launch adds 1 KB of slack)
+  uint8_t* tc_smem = tc_smem_raw + ((1024u - (smem_u32(tc_smem_raw) & 1023u)) & 1023u);
+  const int d = a.dil, RW = LAYOUT ? (128 + 2 * d + 7) / 8 * 8 : 128 + 2 * d, planes = a.cg / 8, nout = a.nout;
+  const uint32_t BSZ = 9u * a.cg * nout * 2, ASZ = LAYOUT ? 3u * RW * 128 : 6u * a.cg * RW, LBOA = 3u * RW * 16;
+  const uint32_t ncols = nout * 2 <= 32 ? 32 : (nout * 2 <= 64 ? 64 : (nout * 2 <= 128 ? 128 : (nout * 2 <= 256 ? 256 : 512)));
+  const int TX = (g.W + 127) / 128;
+  const int64_t T = (int64_t)g.nb * g.H * TX;
+  const int sgn = (MODE == MODE_FWD) ? 1 : -1;
+
+  if (tid == 0) {
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&full_b[i], LAYOUT ? 1 : kTcProducers);
+      mbar_init(&empty_b[i], 1);
+      mbar_init(&accf_b[i], 1);
+      mbar_init(&acce_b[i], kTcEpiWarps);
+    }
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  if (MODE == MODE_FWD)
+    for (int n = tid; n < nout; n += kTcThreads) sbias[n] = a.bias[n];
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&tmem_slot)),
+                 "r"(ncols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+  }
+  // weights of the nine taps: chunk (t, kc, n) at ((t * planes + kc) * nout + n) * 16
+  for (int e = tid; e < 9 * planes * nout; e += kTcThreads) {
+    const int n = e % nout, kc = (e / nout) % planes, t = e / (nout * planes);
+    const bf16* src = (MODE == MODE_FWD) ? a.wsrc + ((int64_t)n * 9 + t) * a.cg + 8 * kc
+                                         : a.wsrc + ((int64_t)t * nout + n) * a.cg + 8 * kc;
+    if (LAYOUT) cp16(tc_smem + (t * nout + n) * 128 + ((kc ^ (n & 7)) << 4), src, true);
+    else cp16(tc_smem + ((t * planes + kc) * nout + n) * 16, src, true);
+  }
+  cp_commit();
+  cp_wait<0>();
+  fence_proxy_async();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_slot;
+  bool aborted = false;
+
+  if (LAYOUT && warp < 2) {
+    // ---------------- TMA producer (one lane) ----------------
+    if (tid == 0) {
+      int i = 0;
+      for (int64_t tile = blockIdx.x; tile < T; tile += gridDim.x, ++i) {
+        const int st = i & 1, k = i >> 1;
+        if (k >= 1 && !role_wait(&empty_b[st], (k - 1) & 1, a.spin_limit, &abort_flag)) { aborted = true; break; }
+        const int j = int(tile % TX);
+        const int64_t rowid = tile / TX;
+        const int y = int(rowid % g.H), img = int(rowid / g.H);
+        mbar_expect_tx(&full_b[st], 3u * RW * 128);
+        const uint32_t dst = smem_u32(tc_smem + BSZ + st * ASZ);
+        for (int r = 0; r < 3; ++r)
+          tma_load_4d(dst + r * RW * 128, &tmap, 0, 128 * j - d, y + (r - 1) * d, img, &full_b[st]);
+      }
+    }
+    __syncwarp();
+  } else if (warp < 2) {
+    // ---------------- producers ----------------
+    // chunk e = ptid + k * 64: plane kc = e % planes (fixed per thread), halo pixel q = e / planes
+    const int ptid = tid, qstep = kTcProducers / planes, kc = ptid % planes;
+    const int total_q = 3 * RW;
+    int i = 0;
+    for (int64_t tile = blockIdx.x; tile < T; tile += gridDim.x, ++i) {
+      const int st = i & 1, k = i >> 1;
+      if (k >= 1 && !role_wait(&empty_b[st], (k - 1) & 1, a.spin_limit, &abort_flag)) { aborted = true; break; }
+      const int j = int(tile % TX);
+      const int64_t rowid = tile / TX;
+      const int y = int(rowid % g.H), x0 = 128 * j;
+      uint8_t* dst0 = tc_smem + BSZ + st * ASZ + kc * LBOA;
+      int q = ptid / planes, r = q / RW, c = q - r * RW;
+      for (; q < total_q; q += qstep) {
+        const int yy = y + (r - 1) * d, xx = x0 - d + c;
+        const bool v = yy >= 0 && yy < g.H && xx >= 0 && xx < g.W;
+        const bf16* src = v ? a.act + ((rowid + (int64_t)(r - 1) * d) * g.W + xx) * a.cg + 8 * kc : a.act;
+        cp16(dst0 + (r * RW + c) * 16, src, v);
+        c += qstep;
+        while (c >= RW) { c -= RW; ++r; }
+      }
+      cp_commit();
+      if (i >= 1) {
+        cp_wait<1>();
+        fence_proxy_async();
+        mbar_arrive(&full_b[(i - 1) & 1]);
+      }
+    }
+    cp_wait<0>();
+    if (i >= 1 && !aborted) {
+      fence_proxy_async();
+      mbar_arrive(&full_b[(i - 1) & 1]);
+    }
+  } else if (warp == 2) {
+    // ---------------- MMA issuer ----------------
+    if (lane == 0) {
+      const uint32_t idesc = idesc_bf16(128, nout);
+      const uint32_t sm_base = smem_u32(tc_smem);
+      int i = 0;
+      for (int64_t tile = blockIdx.x; tile < T; tile += gridDim.x, ++i) {
+        const int st = i & 1, k = i >> 1;
+        if (!role_wait(&full_b[st], k & 1, a.spin_limit, &abort_flag)) { aborted = true; break; }
+        if (k >= 1 && !role_wait(&acce_b[st], (k - 1) & 1, a.spin_limit, &abort_flag)) { aborted = true; break; }
+        tc_fence_after();
+        const uint32_t a0 = sm_base + BSZ + st * ASZ;
+        for (int t = 0; t < 9; ++t) {
+          const int sy = sgn * tap_dy(t), sx = sgn * tap_dx(t);
+          if (LAYOUT) {
+            const uint32_t aoff = a0 + (uint32_t)(((1 + sy) * RW + d + sx * d) * 128);
+            const uint32_t boff = sm_base + (uint32_t)(t * nout * 128);
+            for (int kk = 0; kk < 4; ++kk)
+              tc_mma(tmem + (uint32_t)(st * nout), sdesc_sw128(aoff + 32 * kk), sdesc_sw128(boff + 32 * kk), idesc,
+                     (t | kk) != 0);
+          } else {
+            const uint32_t aoff = a0 + (uint32_t)(((1 + sy) * RW + d + sx * d) * 16);
+            const uint32_t boff = sm_base + (uint32_t)(t * planes * nout * 16);
+            for (int kk = 0; kk < planes / 2; ++kk) {
+              const uint64_t ad = sdesc(aoff + 2 * kk * LBOA, LBOA, 128);
+              const uint64_t bd = sdesc(boff + 2 * kk * nout * 16, nout * 16, 128);
+              tc_mma(tmem + (uint32_t)(st * nout), ad, bd, idesc, (t | kk) != 0);
+            }
+          }
+        }
+        tc_commit(&empty_b[st]);
+        tc_commit(&accf_b[st]);
+      }
+    }
+    __syncwarp();
+  } else {
+    // ---------------- epilogue ----------------
+    const int q4 = warp & 3, chalf = (warp - 3) >> 2;
+    const int m = 32 * q4 + lane;
+    const int cw = nout / 2;                     // columns of this warp: [chalf * cw, chalf * cw + cw)
+    int i = 0;
+    for (int64_t tile = blockIdx.x; tile < T; tile += gridDim.x, ++i) {
+      const int b = i & 1, k = i >> 1;
+      const bool ok_wait = role_wait(&accf_b[b], k & 1, a.spin_limit, &abort_flag);
+      if (!__all_sync(0xffffffffu, ok_wait)) { aborted = true; break; }
+      tc_fence_after();
+      const int j = int(tile % TX);
+      const int64_t rowid = tile / TX;
+      const int x = 128 * j + m;
+      const bool ok = x < g.W;
+      const int64_t p = rowid * g.W + x;
+      const int cend = chalf * cw + cw;
+      int nc = 0;
+      for (int c0 = chalf * cw; c0 < cend; c0 += nc) {
+        float v[32];
+        uint4 sdv[4];
+        nc = cend - c0 >= 32 ? 32 : (cend - c0 >= 16 ? 16 : 8);
+        if (MODE == MODE_BWD_DATA && a.sdprev && ok) {   // silu' of these columns, in flight during the TMEM load
+          const uint4* src = reinterpret_cast<const uint4*>(a.sdprev + p * nout + c0);
+#pragma unroll
+          for (int e = 0; e < 4; ++e)
+            if (8 * e < nc) sdv[e] = src[e];
+        }
+        const uint32_t ta = tmem + ((uint32_t)(32 * q4) << 16) + (uint32_t)(b * nout + c0);
+        if (nc == 32) {
+          tc_ld32(ta, v);
+        } else {
+          for (int e = 0; e < nc; e += 8) tc_ld8(ta + e, v + e);
+        }
+        if (c0 + nc >= cend) {   // the accumulator is in registers: release it to the MMA issuer
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&acce_b[b]);
+        }
+        if (!ok) continue;
+        for (int c1 = 0; c1 < nc; c1 += 8) {
+          const int cc = c0 + c1;
+          if (MODE == MODE_FWD) {
+            float zz[8], sg[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+              zz[e] = v[c1 + e] + sbias[cc + e];
+              sg[e] = __fdividef(1.f, 1.f + __expf(-zz[e]));   // sigmoid, shared by silu and silu'
+            }
+            if (a.z) {
+              float4* zd = reinterpret_cast<float4*>(a.z + p * nout + cc);
+              zd[0] = make_float4(zz[0], zz[1], zz[2], zz[3]);
+              zd[1] = make_float4(zz[4], zz[5], zz[6], zz[7]);
+            }
+            if (a.h) {
+              __nv_bfloat162 hb[4];
+#pragma unroll
+              for (int e = 0; e < 4; ++e)
+                hb[e] = __floats2bfloat162_rn(zz[2 * e] * sg[2 * e], zz[2 * e + 1] * sg[2 * e + 1]);
+              *reinterpret_cast<uint4*>(a.h + p * nout + cc) = *reinterpret_cast<uint4*>(hb);
+            }
+            if (a.sd) {
+              __nv_bfloat162 sb[4];
+#pragma unroll
+              for (int e = 0; e < 4; ++e)
+                sb[e] = __floats2bfloat162_rn(sg[2 * e] * (1.f + zz[2 * e] * (1.f - sg[2 * e])),
+                                              sg[2 * e + 1] * (1.f + zz[2 * e + 1] * (1.f - sg[2 * e + 1])));
+              *reinterpret_cast<uint4*>(a.sd + p * nout + cc) = *reinterpret_cast<uint4*>(sb);
+            }
+          } else {
+            float dd[8];
+            if (a.sdprev) {
+              const uint4 raw = sdv[c1 / 8];
+              const __nv_bfloat162* sp = reinterpret_cast<const __nv_bfloat162*>(&raw);
+#pragma unroll
+              for (int e = 0; e < 4; ++e) {
+                const float2 f = __bfloat1622float2(sp[e]);
+                dd[2 * e] = v[c1 + 2 * e] * f.x;
+                dd[2 * e + 1] = v[c1 + 2 * e + 1] * f.y;
+              }
+            } else {
+#pragma unroll
+              for (int e = 0; e < 8; ++e) dd[e] = v[c1 + e];
+            }
+            __nv_bfloat162 hb[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) hb[e] = __floats2bfloat162_rn(dd[2 * e], dd[2 * e + 1]);
+            *reinterpret_cast<uint4*>(a.dzprev + p * nout + cc) = *reinterpret_cast<uint4*>(hb);
+          }
+        }
+      }
+    }
+  }
+  if (aborted) {
+    abort_flag = 1;
+    atomicOr(a.err, 1);
+  }
+  cp_wait<0>();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(ncols));
+}
+
+// ---------------------------------------------------------------------------
+// Tensor-core weight gradient for 64-in / 64-out layers:
+//     dW[co][t][ci] = sum_p dz[p][co] h[p + d o_t][ci].
+// K = pixels, so both operands are MN-major in their natural channels-last
+// layout: the halo of h (as in the forward kernel) and the tile's dz rows
+// (one TMA box of 128 pixels x 64 channels), both 128-byte swizzled.  One MMA
+// covers two taps: M = 128 rows = (tap t1: ci 0..63, tap t2: ci 0..63), the
+// two halves being the two taps' shifted views of the halo (the descriptor's
+// leading byte offset is their distance), N = 64 (co), K = 16 pixels.  Five
+// tap pairs accumulate in TMEM (5 x 64 FP32 columns) over the CTA's run of
+// tiles.  The last pair's second half reads a block of BF16 ones instead of a
+// tap view, so its rows hold sum_p dz[p][co]: the bias gradient.  The CTA
+// then writes its partial sums (weights, then bias), and k_sum_parts adds the
+// CTAs' parts in a fixed order.
+// ---------------------------------------------------------------------------
+struct WgArgs {
+  Geo g;
+  int dil;
+  float* part;          // [gridDim.x][64 * 9 * 64 + 64]: weight part, then bias part
+  int* err;
+  long long spin_limit;
+};
+constexpr int kWgThreads = 128, kWgMaxParts = 160;
+constexpr size_t kWgSmem = 220 * 1024;    // two stages of halo + dz tile, the ones block, alignment: <= 173 KB
+constexpr uint32_t kWgDz = 128 * 128;     // one dz tile: 128 pixels x 128 bytes
+constexpr int64_t kWgPart = 64 * 9 * 64 + 64;
+
+__global__ void __launch_bounds__(kWgThreads, 1) k_wgrad_tc(const WgArgs a, const __grid_constant__ CUtensorMap tm_h,
+                                                            const __grid_constant__ CUtensorMap tm_dz) {
+  extern __shared__ __align__(1024) uint8_t wg_smem_raw[];
+  __shared__ __align__(8) uint64_t full_b[2], empty_b[2], done_b;
+  __shared__ uint32_t tmem_slot;
+  __shared__ volatile int abort_flag;
+  uint8_t* sm = wg_smem_raw + ((1024u - (smem_u32(wg_smem_raw) & 1023u)) & 1023u);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const Geo& g = a.g;
+  const int d = a.dil, RW = (128 + 2 * d + 7) / 8 * 8;
+  const uint32_t HALO = 3u * RW * 128, STG = HALO + kWgDz;
+  const int TX = (g.W + 127) / 128;
+  const int64_t T = (int64_t)g.nb * g.H * TX;
+  const int64_t t_begin = T * blockIdx.x / gridDim.x, t_end = T * (blockIdx.x + 1) / gridDim.x;
+  if (tid == 0) {
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&full_b[i], 1);
+      mbar_init(&empty_b[i], 1);
+    }
+    mbar_init(&done_b, 1);
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&tmem_slot)),
+                 "r"(512));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+  }
+  // the ones block (16 KB of BF16 1.0) after the two stages
+  {
+    uint4* ones = reinterpret_cast<uint4*>(sm + 2 * STG);
+    const uint32_t one2 = 0x3F803F80u;
+    for (int i = tid; i < (int)(kWgDz / 16); i += kWgThreads) ones[i] = make_uint4(one2, one2, one2, one2);
+  }
+  fence_proxy_async();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_slot;
+  bool aborted = false;
+  const int64_t ntiles = t_end - t_begin;
+
+  if (warp == 0) {
+    if (lane == 0) {   // producer
+      for (int64_t i = 0; i < ntiles; ++i) {
+        const int st = int(i & 1);
+        const int64_t k = i >> 1;
+        if (k >= 1 && !role_wait(&empty_b[st], (uint32_t)((k - 1) & 1), a.spin_limit, &abort_flag)) {
+          aborted = true;
+          break;
+        }
+        const int64_t tile = t_begin + i;
+        const int j = int(tile % TX);
+        const int64_t rowid = tile / TX;
+        const int y = int(rowid % g.H), img = int(rowid / g.H);
+        mbar_expect_tx(&full_b[st], STG);
+        const uint32_t dst = smem_u32(sm + st * STG);
+        for (int r = 0; r < 3; ++r)
+          tma_load_4d(dst + r * RW * 128, &tm_h, 0, 128 * j - d, y + (r - 1) * d, img, &full_b[st]);
+        tma_load_4d(dst + HALO, &tm_dz, 0, 128 * j, y, img, &full_b[st]);
+      }
+    }
+    __syncwarp();
+  } else if (warp == 1) {
+    if (lane == 0) {   // MMA issuer
+      const uint32_t idesc = idesc_bf16(128, 64) | (1u << 15) | (1u << 16);   // A and B MN-major
+      const uint32_t base = smem_u32(sm);
+      for (int64_t i = 0; i < ntiles; ++i) {
+        const int st = int(i & 1);
+        if (!role_wait(&full_b[st], (uint32_t)((i >> 1) & 1), a.spin_limit, &abort_flag)) {
+          aborted = true;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t halo = base + st * STG, dzt = halo + HALO;
+        for (int pi = 0; pi < 5; ++pi) {
+          const int t1 = 2 * pi, t2 = 2 * pi + 1;
+          const uint32_t v1 = halo + (uint32_t)(((1 + tap_dy(t1)) * RW + d + tap_dx(t1) * d) * 128);
+          const uint32_t v2 = pi < 4 ? halo + (uint32_t)(((1 + tap_dy(t2)) * RW + d + tap_dx(t2) * d) * 128)
+                                     : base + 2 * STG;   // ones: the bias gradient
+          for (int kk = 0; kk < 8; ++kk)
+            tc_mma(tmem + (uint32_t)(pi * 64), sdesc_sw128(v1 + kk * 2048, v2 - v1), sdesc_sw128(dzt + kk * 2048),
+                   idesc, (i > 0 || kk > 0) ? 1u : 0u);
+        }
+        tc_commit(&empty_b[st]);
+      }
+      if (!aborted) tc_commit(&done_b);
+    }
+    __syncwarp();
+  }
+  // all four warps: drain the accumulators into this CTA's part
+  if (__syncthreads_or(aborted)) aborted = true;
+  if (!aborted && ntiles > 0) {
+    const bool ok = role_wait(&done_b, 0, a.spin_limit, &abort_flag);
+    if (__syncthreads_or(!ok)) aborted = true;
+  }
+  if (!aborted) {
+    tc_fence_after();
+    float* part = a.part + (int64_t)blockIdx.x * kWgPart;
+    const int r = 32 * warp + lane;          // accumulator row = (tap half, ci)
+    for (int pi = 0; pi < 5; ++pi) {
+      float v[64];
+      if (ntiles > 0) {
+        tc_ld32(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(pi * 64), v);
+        tc_ld32(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(pi * 64 + 32), v + 32);
+      } else {
+        for (int c = 0; c < 64; ++c) v[c] = 0.f;
+      }
+      const int t = 2 * pi + (r >> 6), ci = r & 63;
+      if (t < 9)
+        for (int co = 0; co < 64; ++co) part[((int64_t)co * 9 + t) * 64 + ci] = v[co];
+      else if (r == 64)
+        for (int co = 0; co < 64; ++co) part[64 * 9 * 64 + co] = v[co];
+    }
+  }
+  if (aborted) {
+    abort_flag = 1;
+    if (tid == 0) atomicOr(a.err, 1);
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(512));
+}
+
+// dw[i] += sum over the parts (fixed order) for the weights, db[c] likewise for the bias
+__global__ void k_sum_parts(const float* __restrict__ part, int nparts, float* __restrict__ dw,
+                            float* __restrict__ db) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < kWgPart; i += (int64_t)gridDim.x * blockDim.x) {
+    float acc = 0.f;
+    for (int b = 0; b < nparts; ++b) acc += part[(int64_t)b * kWgPart + i];
+    if (i < 64 * 9 * 64) dw[i] += acc;
+    else db[i - 64 * 9 * 64] += acc;
+  }
 }
 
 // WT[t][ci][co] = W[co][t][ci] (BF16), the backward-data operand layout
@@ -528,36 +1101,61 @@ __global__ void k_project(float2* __restrict__ out, int64_t HW, const double* __
   }
 }
 
-// complex state -> 2-channel BF16 input; also FP32 copy of the state for the residual
-__global__ void k_pack_input(const float2* __restrict__ psi, int64_t P, bf16* __restrict__ h) {
-  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < P; p += (int64_t)gridDim.x * blockDim.x) {
-    const float2 v = psi[p];
-    h[2 * p] = __float2bfloat16_rn(v.x);
-    h[2 * p + 1] = __float2bfloat16_rn(v.y);
+// The two-channel ends of the network run as pc-channel layers (pc = C when C
+// is 16, 32, 48 or 64, else 16): the input activation carries (Re, Im, 0 ...),
+// the last layer computes pc outputs of which channels 2.. have zero weights
+// and bias, and its output gradient is written with the same pc stride.
+// Every layer then fits the same kernels as the inner ones; the padding adds
+// exact zeros only.
+__host__ __device__ inline int pad_width(int C) { return (C % 16 == 0 && C <= 64) ? C : 16; }
+
+// complex state -> pc-channel BF16 input (Re, Im, zeros); one thread per 16-byte chunk
+__global__ void k_pack_input(const float2* __restrict__ psi, int64_t P, int pc, bf16* __restrict__ h) {
+  const int cpp = pc / 8;
+  uint4* dst = reinterpret_cast<uint4*>(h);
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < P * cpp; q += (int64_t)gridDim.x * blockDim.x) {
+    uint4 v = make_uint4(0u, 0u, 0u, 0u);
+    if (q % cpp == 0) {
+      const float2 z = psi[q / cpp];
+      const __nv_bfloat162 re_im = __floats2bfloat162_rn(z.x, z.y);
+      v.x = *reinterpret_cast<const uint32_t*>(&re_im);
+    }
+    dst[q] = v;
   }
 }
 
-// psi_out = psi_in + y
-__global__ void k_residual(const float2* __restrict__ psi, const float* __restrict__ y, int64_t P,
+// psi_out = psi_in + (y_0 + i y_1), y with a pc-channel row stride
+__global__ void k_residual(const float2* __restrict__ psi, const float* __restrict__ y, int64_t P, int pc,
                            float2* __restrict__ out) {
   for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < P; p += (int64_t)gridDim.x * blockDim.x) {
     const float2 v = psi[p];
-    out[p] = make_float2(v.x + y[2 * p], v.y + y[2 * p + 1]);
+    const float2 d = *reinterpret_cast<const float2*>(y + p * pc);
+    out[p] = make_float2(v.x + d.x, v.y + d.y);
   }
 }
 
-// MSE loss (FP64 partial sums) and its gradient w.r.t. y, written as BF16 dz of the last layer
+// MSE loss (FP64 partial sums) and its gradient w.r.t. y, written as the BF16
+// output gradient of the last layer (pc-channel rows, channels 2.. zero); one
+// thread per 16-byte chunk of that gradient
 __global__ void k_mse(const float2* __restrict__ psi, const float* __restrict__ y, const float2* __restrict__ target,
-                      int64_t P, bf16* __restrict__ dz, double* __restrict__ loss_acc) {
+                      int64_t P, int pc, bf16* __restrict__ dz, double* __restrict__ loss_acc) {
   __shared__ double red[256];
   double s = 0.0;
   const float scale = 2.f / float(2 * P);
-  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < P; p += (int64_t)gridDim.x * blockDim.x) {
-    const float2 v = psi[p], t = target[p];
-    const float ex = v.x + y[2 * p] - t.x, ey = v.y + y[2 * p + 1] - t.y;
-    s += double(ex) * ex + double(ey) * ey;
-    dz[2 * p] = __float2bfloat16_rn(scale * ex);
-    dz[2 * p + 1] = __float2bfloat16_rn(scale * ey);
+  const int cpp = pc / 8;
+  uint4* dst = reinterpret_cast<uint4*>(dz);
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < P * cpp; q += (int64_t)gridDim.x * blockDim.x) {
+    uint4 v = make_uint4(0u, 0u, 0u, 0u);
+    if (q % cpp == 0) {
+      const int64_t p = q / cpp;
+      const float2 u = psi[p], t = target[p];
+      const float2 d = *reinterpret_cast<const float2*>(y + p * pc);
+      const float ex = u.x + d.x - t.x, ey = u.y + d.y - t.y;
+      s += double(ex) * ex + double(ey) * ey;
+      const __nv_bfloat162 g = __floats2bfloat162_rn(scale * ex, scale * ey);
+      v.x = *reinterpret_cast<const uint32_t*>(&g);
+    }
+    dst[q] = v;
   }
   red[threadIdx.x] = s;
   __syncthreads();
@@ -568,18 +1166,65 @@ __global__ void k_mse(const float2* __restrict__ psi, const float* __restrict__ 
   if (threadIdx.x == 0) atomicAdd(loss_acc, red[0] / double(2 * P));
 }
 
-// db[c] = sum over pixels of dz[p, c]  (one block per channel)
-__global__ void k_bias_grad(const bf16* __restrict__ dz, int64_t P, int C, float* __restrict__ db) {
+// db[c] += sum over pixels of dz[p * stride + c] for c < creal (stride <= 256;
+// 256 threads: thread t takes channel t % stride of every (256 / stride)-th pixel)
+__global__ void k_bias_grad(const bf16* __restrict__ dz, int64_t P, int stride, int creal, float* __restrict__ db) {
   __shared__ float red[256];
+  const int groups = 256 / stride, c = threadIdx.x % stride, gi = threadIdx.x / stride;
   float s = 0.f;
-  for (int64_t p = threadIdx.x; p < P; p += blockDim.x) s += __bfloat162float(dz[p * C + blockIdx.x]);
+  if (gi < groups)
+    for (int64_t p = (int64_t)blockIdx.x * groups + gi; p < P; p += (int64_t)gridDim.x * groups)
+      s += __bfloat162float(dz[p * stride + c]);
   red[threadIdx.x] = s;
   __syncthreads();
-  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-    if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
-    __syncthreads();
+  if ((int)threadIdx.x < stride) {
+    float t = 0.f;
+    for (int g = 0; g < groups; ++g) t += red[g * stride + threadIdx.x];
+    if ((int)threadIdx.x < creal) atomicAdd(&db[threadIdx.x], t);
   }
-  if (threadIdx.x == 0) db[blockIdx.x] += red[0];
+}
+
+// Padded operand copies of the end layers (BF16 weights from the BF16 copy, FP32 bias):
+//   w0[co][t][c]   = W_0[co][t][c] for c < 2, else 0            (C x 9 x pc)
+//   wl[o][t][ci]   = W_{L-1}[o][t][ci] for o < 2, else 0        (pc x 9 x C)
+//   wlt[t][ci][o]  = the same, transposed for backward-data     (9 x C x pc)
+//   bl[o]          = b_{L-1}[o] for o < 2, else 0
+__global__ void k_pad_ends(const bf16* __restrict__ w0src, const bf16* __restrict__ wlsrc,
+                           const float* __restrict__ blsrc, int C, int pc, bf16* __restrict__ w0,
+                           bf16* __restrict__ wl, bf16* __restrict__ wlt, float* __restrict__ bl) {
+  const bf16 zero = __float2bfloat16_rn(0.f);
+  const int64_t n = (int64_t)C * 9 * pc;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    {   // w0, i = (co * 9 + t) * pc + c
+      const int c = int(i % pc);
+      const int64_t ct = i / pc;
+      w0[i] = c < 2 ? w0src[ct * 2 + c] : zero;
+    }
+    {   // wl, i = (o * 9 + t) * C + ci
+      const int64_t o = i / (9 * (int64_t)C);
+      wl[i] = o < 2 ? wlsrc[i] : zero;
+    }
+    {   // wlt, i = (t * C + ci) * pc + o
+      const int o = int(i % pc);
+      const int64_t tc = i / pc;
+      const int ci = int(tc % C), t = int(tc / C);
+      wlt[i] = o < 2 ? wlsrc[((int64_t)o * 9 + t) * C + ci] : zero;
+    }
+    if (i < pc) bl[i] = i < 2 ? blsrc[i] : 0.f;
+  }
+}
+
+// grad += the real part of a padded layer's gradient (scratch: weights, then pc bias slots):
+//   first layer: W[(co * 9 + t) * 2 + c] += scr[(co * 9 + t) * pc + c] (c < 2); b[co] += scr[nw + co], co < C
+//   last layer:  W[i] += scr[i] for i < 2 * 9 * C (rows 0, 1);             b[o] += scr[nw + o], o < 2
+__global__ void k_unpad_grad(const float* __restrict__ scr, float* __restrict__ dw, float* __restrict__ db, int C,
+                             int pc, int first) {
+  const int64_t nw = (int64_t)C * 9 * pc, n = (int64_t)18 * C;
+  const int nb = first ? C : 2;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n + nb; i += (int64_t)gridDim.x * blockDim.x) {
+    if (i < n) dw[i] += first ? scr[(i / 2) * pc + (i % 2)] : scr[i];
+    else db[i - n] += scr[nw + (i - n)];
+  }
 }
 
 // Adam step on the FP32 masters, refreshing the BF16 copies
@@ -635,10 +1280,21 @@ struct nlse_sur {
   float* m2;
   double* loss;
   double* mass_part;              // [max_batch][kMassBlocks][2]
-  bf16* hin;                      // input activation, 2 channels
-  std::vector<float*> z;          // pre-activations, layer 0..L-1 (last: y, 2 channels)
+  int pc;                         // padded width of the two-channel ends
+  bf16* hin;                      // input activation, pc channels (Re, Im, zeros)
+  bf16* pw0;                      // padded first-layer weights [C][9][pc]
+  bf16* pwL;                      // padded last-layer weights [pc][9][C]
+  bf16* pwLT;                     // its backward-data layout [9][C][pc]
+  float* pbL;                     // padded last-layer bias [pc]
+  float* wscr;                    // padded-layer gradient scratch [C * 9 * pc] weights + [pc] bias
+  float* wgpart;                  // per-CTA weight-gradient parts of the tensor-core kernel (C = 64 only)
+  float* y;                       // last layer's output, pc-channel rows (FP32)
+  std::vector<bf16*> sd;          // silu'(z) of layers 0..L-2 (BF16; training)
   std::vector<bf16*> h;           // activations, layer 0..L-2
-  bf16* dzA;                      // gradient ping-pong buffers (C channels)
+  int* err;                       // device flag: a bounded wait in a tensor-core kernel ran out
+  int num_sms;
+  int use_tc;                     // tcgen05 kernels for eligible forward / backward-data layers
+  bf16* dzA;                      // gradient ping-pong buffers (max(C, pc) channels)
   bf16* dzB;
   int64_t adam_t;
 };
@@ -668,12 +1324,55 @@ size_t ws_bytes(int H, int W, int C, int L, int max_batch) {
   off = al(off + np * 4);            // m2
   off = al(off + 64);                // loss
   off = al(off + (size_t)max_batch * kMassBlocks * 2 * 8);   // mass_part
-  off = al(off + P * 2 * 2);         // hin
-  for (int l = 0; l < L; ++l) off = al(off + P * (l == L - 1 ? 2 : C) * 4);   // z
-  for (int l = 0; l < L - 1; ++l) off = al(off + P * C * 2);                   // h
-  off = al(off + P * C * 2);         // dzA
-  off = al(off + P * C * 2);         // dzB
+  off = al(off + 16);                // err
+  const int pc = pad_width(C);
+  off = al(off + P * pc * 2);        // hin
+  off = al(off + (size_t)C * 9 * pc * 2);     // pw0
+  off = al(off + (size_t)C * 9 * pc * 2);     // pwL
+  off = al(off + (size_t)C * 9 * pc * 2);     // pwLT
+  off = al(off + pc * 4);                     // pbL
+  off = al(off + ((size_t)C * 9 * pc + pc) * 4);   // wscr
+  off = al(off + (C == 64 ? (size_t)kWgMaxParts * kWgPart * 4 : 0));   // wgpart
+  off = al(off + P * pc * 4);                                   // y
+  for (int l = 0; l < L - 1; ++l) off = al(off + P * C * 2);    // sd
+  for (int l = 0; l < L - 1; ++l) off = al(off + P * C * 2);    // h
+  const int64_t cz = C > pc ? C : pc;
+  off = al(off + P * cz * 2);        // dzA
+  off = al(off + P * cz * 2);        // dzB
   return off;
+}
+
+// layout 1 (TMA, 128-byte swizzle) serves 64 gathered channels; layout 0 the rest
+int tc_layout(int cg) { return cg == 64 ? 1 : 0; }
+
+size_t tc_smem_bytes(int cg, int nout, int dil) {
+  const size_t halo = tc_layout(cg) ? (size_t)3 * ((128 + 2 * dil + 7) / 8 * 8) * 128
+                                    : (size_t)6 * cg * (128 + 2 * dil);
+  return (size_t)9 * cg * nout * 2 + 2 * halo + 1024;
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// 4D map over a channels-last BF16 activation [nb][H][W][64]: box of 64
+// channels x rw pixels of one row, 128-byte swizzle, zero fill outside.
+bool halo_tmap(CUtensorMap* m, const bf16* act, int nb, int H, int W, int rw) {
+  EncodeTiledFn fn = reinterpret_cast<EncodeTiledFn>(nlse::tensor_map_encoder());
+  if (!fn) return false;
+  const cuuint64_t dims[4] = {64, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)nb};
+  const cuuint64_t strides[3] = {128, (cuuint64_t)W * 128, (cuuint64_t)H * W * 128};
+  const cuuint32_t box[4] = {64, (cuuint32_t)rw, 1, 1};
+  const cuuint32_t es[4] = {1, 1, 1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<bf16*>(act), dims, strides, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// gathered channels: a multiple of 16 whose 8-channel planes divide the 64 copying threads
+bool tc_ok(int cg, int nout, int dil) {
+  return cg % 16 == 0 && kTcProducers % (cg / 8) == 0 && nout % 16 == 0 && nout >= 16 && nout <= 256 &&
+         dil <= 16 && tc_smem_bytes(cg, nout, dil) <= 220 * 1024;
 }
 
 bool fast_ok(int mode, int cin, int cout) {
@@ -682,25 +1381,105 @@ bool fast_ok(int mode, int cin, int cout) {
   return cout % 8 == 0 && cin % 8 == 0;
 }
 
+// Operands of layer l as the kernels see them (the end layers padded to 16 channels).
+struct LayerOps {
+  int cin, cout;
+  const bf16* w;
+  const bf16* wt;
+  const float* bias;
+  float* dw;
+  float* db;
+};
+LayerOps layer_ops(const nlse_sur* s, int l) {
+  const bool first = l == 0, last = l == s->L - 1;
+  LayerOps o;
+  o.cin = first ? s->pc : s->C;
+  o.cout = last ? s->pc : s->C;
+  o.w = first ? s->pw0 : (last ? s->pwL : s->pbf + s->w_off[l]);
+  o.wt = last ? s->pwLT : s->pbfT + s->w_off[l];
+  o.bias = last ? s->pbL : s->params + s->b_off[l];
+  o.dw = (first || last) ? s->wscr : s->grad + s->w_off[l];
+  o.db = (first || last) ? s->wscr + (int64_t)s->C * 9 * s->pc : s->grad + s->b_off[l];
+  return o;
+}
+
+// Returns through *bias_done whether the weight-gradient kernel also produced the bias gradient.
 cudaError_t conv(const nlse_sur* s, int mode, int l, int nb, const bf16* x, const bf16* dz, float* z, bf16* h,
-                 const float* zprev, bf16* dzprev, float* dw) {
+                 bf16* sd, const bf16* sdprev, bf16* dzprev, bool* bias_done = nullptr) {
+  if (bias_done) *bias_done = false;
+  const LayerOps o = layer_ops(s, l);
   ConvArgs a;
   memset(&a, 0, sizeof(a));
   a.g = {nb, s->H, s->W};
-  a.cin = cin_of(s, l);
-  a.cout = cout_of(s, l);
+  a.cin = o.cin;
+  a.cout = o.cout;
   a.dil = s->dil[l];
   a.x = x;
   a.dz = dz;
-  a.w = s->pbf + s->w_off[l];
-  a.bias = s->params + s->b_off[l];
+  a.w = o.w;
+  a.bias = o.bias;
   a.z = z;
   a.h = h;
-  a.zprev = zprev;
+  a.sd = sd;
+  a.sdprev = sdprev;
   a.dzprev = dzprev;
-  a.dw = dw;
+  a.dw = o.dw;
   const int64_t P = (int64_t)nb * s->H * s->W;
-  const bf16* wt = s->pbfT + s->w_off[l];
+  const bf16* wt = o.wt;
+  if (s->use_tc && mode != MODE_WGRAD) {
+    const int cg = mode == MODE_FWD ? a.cin : a.cout, nout = mode == MODE_FWD ? a.cout : a.cin;
+    if (tc_ok(cg, nout, a.dil)) {
+      TcArgs t;
+      memset(&t, 0, sizeof(t));
+      t.g = a.g;
+      t.cg = cg;
+      t.nout = nout;
+      t.dil = a.dil;
+      t.act = mode == MODE_FWD ? x : dz;
+      t.wsrc = mode == MODE_FWD ? a.w : wt;
+      t.bias = a.bias;
+      t.z = z;
+      t.h = h;
+      t.sd = sd;
+      t.sdprev = sdprev;
+      t.dzprev = dzprev;
+      t.err = s->err;
+      t.spin_limit = 1ll << 24;
+      const int64_t tiles = (int64_t)nb * s->H * ((s->W + 127) / 128);
+      const size_t smem = tc_smem_bytes(cg, nout, a.dil);
+      const int64_t per_sm = smem <= 100 * 1024 ? 2 : 1;
+      const unsigned grid = (unsigned)(tiles < s->num_sms * per_sm ? tiles : s->num_sms * per_sm);
+      CUtensorMap tm;
+      memset(&tm, 0, sizeof(tm));
+      if (tc_layout(cg)) {
+        if (!halo_tmap(&tm, t.act, nb, s->H, s->W, (128 + 2 * a.dil + 7) / 8 * 8)) return cudaErrorInvalidValue;
+        if (mode == MODE_FWD) k_conv_tc<MODE_FWD, 1><<<grid, kTcThreads, smem, s->stream>>>(t, tm);
+        else k_conv_tc<MODE_BWD_DATA, 1><<<grid, kTcThreads, smem, s->stream>>>(t, tm);
+      } else {
+        if (mode == MODE_FWD) k_conv_tc<MODE_FWD, 0><<<grid, kTcThreads, smem, s->stream>>>(t, tm);
+        else k_conv_tc<MODE_BWD_DATA, 0><<<grid, kTcThreads, smem, s->stream>>>(t, tm);
+      }
+      return cudaGetLastError();
+    }
+  }
+  if (s->use_tc && mode == MODE_WGRAD && a.cin == 64 && a.cout == 64 && a.dil <= 16) {
+    const int rw = (128 + 2 * a.dil + 7) / 8 * 8;
+    CUtensorMap th, tz;
+    if (!halo_tmap(&th, x, nb, s->H, s->W, rw) || !halo_tmap(&tz, dz, nb, s->H, s->W, 128))
+      return cudaErrorInvalidValue;
+    WgArgs w;
+    memset(&w, 0, sizeof(w));
+    w.g = a.g;
+    w.dil = a.dil;
+    w.part = s->wgpart;
+    w.err = s->err;
+    w.spin_limit = 1ll << 24;
+    const int grid = s->num_sms < kWgMaxParts ? s->num_sms : kWgMaxParts;
+    k_wgrad_tc<<<grid, kWgThreads, kWgSmem, s->stream>>>(w, th, tz);
+    k_sum_parts<<<grid1d(kWgPart), 256, 0, s->stream>>>(s->wgpart, grid, a.dw, layer_ops(s, l).db);
+    if (bias_done) *bias_done = true;
+    return cudaGetLastError();
+  }
   if (fast_ok(mode, a.cin, a.cout)) {
     if (mode == MODE_FWD) {
       dim3 grid((unsigned)((P + 127) / 128), (unsigned)((a.cout + 63) / 64));
@@ -735,25 +1514,29 @@ cudaError_t conv(const nlse_sur* s, int mode, int l, int nb, const bf16* x, cons
   return cudaGetLastError();
 }
 
-// BF16 copies (and the transposed copies) of the FP32 masters
+// BF16 copies (and the transposed and padded copies) of the FP32 masters
 cudaError_t refresh_bf16(const nlse_sur* s, bool copy) {
   if (copy) k_to_bf16<<<grid1d(s->nparam), 256, 0, s->stream>>>(s->params, s->pbf, s->nparam);
-  for (int l = 0; l < s->L; ++l) {
-    const int ci = cin_of(s, l), co = cout_of(s, l);
-    k_transpose_w<<<grid1d((int64_t)co * 9 * ci), 256, 0, s->stream>>>(s->pbf + s->w_off[l], s->pbfT + s->w_off[l],
-                                                                     ci, co);
-  }
+  for (int l = 1; l < s->L - 1; ++l)
+    k_transpose_w<<<grid1d((int64_t)s->C * 9 * s->C), 256, 0, s->stream>>>(s->pbf + s->w_off[l],
+                                                                          s->pbfT + s->w_off[l], s->C, s->C);
+  k_pad_ends<<<grid1d((int64_t)s->C * 9 * s->pc), 256, 0, s->stream>>>(
+      s->pbf + s->w_off[0], s->pbf + s->w_off[s->L - 1], s->params + s->b_off[s->L - 1], s->C, s->pc, s->pw0,
+      s->pwL, s->pwLT, s->pbL);
   return cudaGetLastError();
 }
 
-cudaError_t forward(const nlse_sur* s, int nb, const float2* psi_in) {
+// training = false (inference): the inner layers keep only silu(z); true: also silu'(z)
+cudaError_t forward(const nlse_sur* s, int nb, const float2* psi_in, bool training) {
   const int64_t P = (int64_t)nb * s->H * s->W;
-  k_pack_input<<<grid1d(P), 256, 0, s->stream>>>(psi_in, P, s->hin);
+  k_pack_input<<<grid1d(P * s->pc / 8), 256, 0, s->stream>>>(psi_in, P, s->pc, s->hin);
   cudaError_t e = cudaGetLastError();
   const bf16* x = s->hin;
   for (int l = 0; l < s->L && e == cudaSuccess; ++l) {
-    bf16* h = (l < s->L - 1) ? s->h[l] : nullptr;
-    e = conv(s, MODE_FWD, l, nb, x, nullptr, s->z[l], h, nullptr, nullptr, nullptr);
+    const bool last = l == s->L - 1;
+    bf16* h = last ? nullptr : s->h[l];
+    e = conv(s, MODE_FWD, l, nb, x, nullptr, last ? s->y : nullptr, h, (training && !last) ? s->sd[l] : nullptr,
+             nullptr, nullptr);
     x = h;
   }
   return e;
@@ -766,26 +1549,57 @@ cudaError_t backward(const nlse_sur* s, int nb, const float2* psi_in, const floa
   if (e == cudaSuccess) e = cudaMemsetAsync(s->loss, 0, sizeof(double), s->stream);
   if (e != cudaSuccess) return e;
   bf16* dz = s->dzA;   // gradient w.r.t. the current layer's pre-activation
-  k_mse<<<grid1d(P), 256, 0, s->stream>>>(psi_in, s->z[s->L - 1], target, P, dz, s->loss);
+  k_mse<<<grid1d(P * s->pc / 8), 256, 0, s->stream>>>(psi_in, s->y, target, P, s->pc, dz, s->loss);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   for (int l = s->L - 1; l >= 0 && e == cudaSuccess; --l) {
-    const bf16* xin = (l == 0) ? s->hin : s->h[l - 1];
-    e = conv(s, MODE_WGRAD, l, nb, xin, dz, nullptr, nullptr, nullptr, nullptr, s->grad + s->w_off[l]);
+    const bool first = l == 0, last = l == s->L - 1;
+    const LayerOps o = layer_ops(s, l);
+    const bf16* xin = first ? s->hin : s->h[l - 1];
+    if (first || last)
+      e = cudaMemsetAsync(s->wscr, 0, sizeof(float) * ((size_t)9 * s->pc * s->C + s->pc), s->stream);
+    bool bias_done = false;
+    if (e == cudaSuccess) e = conv(s, MODE_WGRAD, l, nb, xin, dz, nullptr, nullptr, nullptr, nullptr, nullptr, &bias_done);
     if (e != cudaSuccess) break;
-    k_bias_grad<<<cout_of(s, l), 256, 0, s->stream>>>(dz, P, cout_of(s, l), s->grad + s->b_off[l]);
+    if (!bias_done) k_bias_grad<<<4 * s->num_sms, 256, 0, s->stream>>>(dz, P, o.cout, o.cout, o.db);
+    if (first || last)
+      k_unpad_grad<<<grid1d((int64_t)18 * s->C + s->C), 256, 0, s->stream>>>(
+          s->wscr, s->grad + s->w_off[l], s->grad + s->b_off[l], s->C, s->pc, first ? 1 : 0);
     if ((e = cudaGetLastError()) != cudaSuccess) break;
     if (l > 0) {
       bf16* dzp = (dz == s->dzA) ? s->dzB : s->dzA;
-      e = conv(s, MODE_BWD_DATA, l, nb, nullptr, dz, nullptr, nullptr, s->z[l - 1], dzp, nullptr);
+      e = conv(s, MODE_BWD_DATA, l, nb, nullptr, dz, nullptr, nullptr, nullptr, s->sd[l - 1], dzp);
       dz = dzp;
     }
   }
   return e;
 }
 
+// Read and clear the device timeout flag (the stream must be idle).
+bool take_err(const nlse_sur* s) {
+  int v = 0;
+  if (cudaMemcpy(&v, s->err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return false;
+  if (v) cudaMemset(s->err, 0, sizeof(int));
+  return v != 0;
+}
+
 }  // namespace
 
 extern "C" {
+
+int nlse_sur_set_kernel(nlse_sur_t s, int tensor_core_gen) {
+  if (!s) return sfail(NLSE_EINVAL, "NULL surrogate");
+  if (tensor_core_gen != 0 && tensor_core_gen != 1) return sfail(NLSE_EINVAL, "kernel choice must be 0 or 1");
+  s->use_tc = tensor_core_gen;
+  return NLSE_OK;
+}
+
+int nlse_sur_sync(nlse_sur_t s) {
+  if (!s) return sfail(NLSE_EINVAL, "NULL surrogate");
+  cudaError_t e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) return sfail(NLSE_ECUDA, cudaGetErrorString(e));
+  if (take_err(s)) return sfail(NLSE_ETIMEOUT, "a tensor-core convolution wait ran out");
+  return NLSE_OK;
+}
 
 size_t nlse_sur_param_count(int channels, int layers) {
   if (channels < 1 || channels > 256 || layers < 2 || layers > kMaxLayers) return 0;
@@ -832,13 +1646,39 @@ int nlse_sur_create(nlse_sur_t* out, int H, int W, int channels, int layers, con
   s->m2 = (float*)(base + o); o = al(o + s->nparam * 4);
   s->loss = (double*)(base + o); o = al(o + 64);
   s->mass_part = (double*)(base + o); o = al(o + (size_t)max_batch * kMassBlocks * 2 * 8);
-  s->hin = (bf16*)(base + o); o = al(o + P * 2 * 2);
-  for (int l = 0; l < layers; ++l) { s->z.push_back((float*)(base + o)); o = al(o + P * cout_of(s, l) * 4); }
+  s->err = (int*)(base + o); o = al(o + 16);
+  s->pc = pad_width(channels);
+  const int pc = s->pc;
+  s->hin = (bf16*)(base + o); o = al(o + P * pc * 2);
+  s->pw0 = (bf16*)(base + o); o = al(o + (size_t)channels * 9 * pc * 2);
+  s->pwL = (bf16*)(base + o); o = al(o + (size_t)channels * 9 * pc * 2);
+  s->pwLT = (bf16*)(base + o); o = al(o + (size_t)channels * 9 * pc * 2);
+  s->pbL = (float*)(base + o); o = al(o + pc * 4);
+  s->wscr = (float*)(base + o); o = al(o + ((size_t)channels * 9 * pc + pc) * 4);
+  s->wgpart = (float*)(base + o); o = al(o + (channels == 64 ? (size_t)kWgMaxParts * kWgPart * 4 : 0));
+  s->y = (float*)(base + o); o = al(o + P * pc * 4);
+  for (int l = 0; l < layers - 1; ++l) { s->sd.push_back((bf16*)(base + o)); o = al(o + P * channels * 2); }
   for (int l = 0; l < layers - 1; ++l) { s->h.push_back((bf16*)(base + o)); o = al(o + P * channels * 2); }
-  s->dzA = (bf16*)(base + o); o = al(o + P * channels * 2);
-  s->dzB = (bf16*)(base + o); o = al(o + P * channels * 2);
+  const int64_t cz = channels > pc ? channels : pc;
+  s->dzA = (bf16*)(base + o); o = al(o + P * cz * 2);
+  s->dzB = (bf16*)(base + o); o = al(o + P * cz * 2);
   s->adam_t = 0;
-  cudaError_t e = cudaMemsetAsync(s->m1, 0, s->nparam * 4, s->stream);
+  int dev = 0;
+  cudaGetDevice(&dev);
+  s->num_sms = 1;
+  cudaDeviceGetAttribute(&s->num_sms, cudaDevAttrMultiProcessorCount, dev);
+  s->use_tc = 1;
+  cudaError_t e = cudaSuccess;
+  {
+    const void* fns[4] = {(const void*)k_conv_tc<MODE_FWD, 0>, (const void*)k_conv_tc<MODE_BWD_DATA, 0>,
+                          (const void*)k_conv_tc<MODE_FWD, 1>, (const void*)k_conv_tc<MODE_BWD_DATA, 1>};
+    for (int i = 0; i < 4 && e == cudaSuccess; ++i)
+      e = cudaFuncSetAttribute(fns[i], cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute((const void*)k_wgrad_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWgSmem);
+  }
+  if (e == cudaSuccess) e = cudaMemsetAsync(s->err, 0, sizeof(int), s->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(s->m1, 0, s->nparam * 4, s->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(s->m2, 0, s->nparam * 4, s->stream);
   if (e == cudaSuccess) e = refresh_bf16(s, true);
   if (e != cudaSuccess) {
@@ -876,10 +1716,10 @@ int nlse_sur_sync_params(nlse_sur_t s) {
 int nlse_sur_forward(nlse_sur_t s, int nb, const void* psi_in, void* psi_out, int project_mass) {
   if (!s || !psi_in || !psi_out) return sfail(NLSE_EINVAL, "NULL argument");
   if (nb < 1 || nb > s->max_batch) return sfail(NLSE_EINVAL, "batch outside 1..max_batch");
-  cudaError_t e = forward(s, nb, (const float2*)psi_in);
+  cudaError_t e = forward(s, nb, (const float2*)psi_in, false);
   if (e == cudaSuccess) {
     const int64_t P = (int64_t)nb * s->H * s->W;
-    k_residual<<<grid1d(P), 256, 0, s->stream>>>((const float2*)psi_in, s->z[s->L - 1], P, (float2*)psi_out);
+    k_residual<<<grid1d(P), 256, 0, s->stream>>>((const float2*)psi_in, s->y, P, s->pc, (float2*)psi_out);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess && project_mass) {
@@ -896,7 +1736,7 @@ int nlse_sur_gradients(nlse_sur_t s, int nb, const void* psi_in, const void* psi
                        double* loss_out) {
   if (!s || !psi_in || !psi_target) return sfail(NLSE_EINVAL, "NULL argument");
   if (nb < 1 || nb > s->max_batch) return sfail(NLSE_EINVAL, "batch outside 1..max_batch");
-  cudaError_t e = forward(s, nb, (const float2*)psi_in);
+  cudaError_t e = forward(s, nb, (const float2*)psi_in, true);
   if (e == cudaSuccess) e = backward(s, nb, (const float2*)psi_in, (const float2*)psi_target);
   if (e == cudaSuccess && grad_out)
     e = cudaMemcpyAsync(grad_out, s->grad, sizeof(float) * s->nparam, cudaMemcpyDeviceToDevice, s->stream);
@@ -905,6 +1745,7 @@ int nlse_sur_gradients(nlse_sur_t s, int nb, const void* psi_in, const void* psi
     e = cudaMemcpyAsync(&l, s->loss, sizeof(double), cudaMemcpyDeviceToHost, s->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
     *loss_out = l;
+    if (e == cudaSuccess && take_err(s)) return sfail(NLSE_ETIMEOUT, "a tensor-core convolution wait ran out");
   }
   return e == cudaSuccess ? NLSE_OK : sfail(NLSE_ECUDA, cudaGetErrorString(e));
 }
@@ -924,6 +1765,7 @@ int nlse_sur_train_step(nlse_sur_t s, int nb, const void* psi_in, const void* ps
     e = cudaMemcpyAsync(&l, s->loss, sizeof(double), cudaMemcpyDeviceToHost, s->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
     *loss_out = l;
+    if (e == cudaSuccess && take_err(s)) return sfail(NLSE_ETIMEOUT, "a tensor-core convolution wait ran out");
   }
   return e == cudaSuccess ? NLSE_OK : sfail(NLSE_ECUDA, cudaGetErrorString(e));
 }

@@ -107,6 +107,13 @@ class Surrogate:
                                              ctypes.byref(loss) if want_loss else None))
         return loss.value if want_loss else None
 
+    def set_kernel(self, tensor_core_gen: int) -> None:
+        """1: tcgen05 kernel for eligible forward / backward-data convolutions; 0: mma.sync only."""
+        L.check(self.lib.nlse_sur_set_kernel(self.s, int(tensor_core_gen)))
+
+    def sync(self) -> None:
+        L.check(self.lib.nlse_sur_sync(self.s))
+
     def close(self):
         if getattr(self, "s", None):
             self.lib.nlse_sur_destroy(self.s)

@@ -26,13 +26,25 @@ def small_net(C=16, L=4, dil=(1, 2, 3, 1), H=24, Wd=28, nb=2, seed=11):
     return sur, psi, target, C, L, dil
 
 
-# C = 16: every inner layer on the cp.async/ldmatrix kernels; C = 12: the generic kernel
-SHAPES = [dict(C=16, L=4, dil=(1, 2, 3, 1)), dict(C=12, L=3, dil=(2, 1, 1))]
+# (shape, kernel choice): C = 16 / 32 with the tcgen05 kernel (tc=1) on the inner
+# forward and backward-data convolutions and the cp.async/ldmatrix mma.sync
+# kernels elsewhere, or mma.sync everywhere (tc=0); C = 12: the generic kernel.
+SHAPES = [(dict(C=16, L=4, dil=(1, 2, 3, 1)), 1), (dict(C=16, L=4, dil=(1, 2, 3, 1)), 0),
+          (dict(C=32, L=4, dil=(1, 8, 5, 1), H=20, Wd=150, nb=3), 1), (dict(C=12, L=3, dil=(2, 1, 1)), 1),
+          (dict(C=64, L=4, dil=(1, 3, 16, 1), H=18, Wd=140, nb=2), 1),
+          (dict(C=64, L=4, dil=(1, 3, 16, 1), H=18, Wd=140, nb=2), 0)]
+IDS = ["tc-16", "mma-16", "tc-32-wide", "generic-12", "tc-64-tma", "mma-64"]
 
 
-@pytest.mark.parametrize("shape", SHAPES, ids=["fast", "generic"])
-def test_forward_matches_reference(shape):
+def make(shape, tc):
     sur, psi, target, C, L, dil = small_net(**shape)
+    sur.set_kernel(tc)
+    return sur, psi, target, C, L, dil
+
+
+@pytest.mark.parametrize("shape,tc", SHAPES, ids=IDS)
+def test_forward_matches_reference(shape, tc):
+    sur, psi, target, C, L, dil = make(shape, tc)
     params = bf16_round(sur.params.cpu().numpy())
     ref, _, _ = S.forward(params, psi, C, L, dil)
     x = torch.as_tensor(psi, dtype=torch.complex64).cuda()
@@ -58,16 +70,17 @@ def test_forward_rejects_bad_batches():
         sur.gradients(x, x[:1])
 
 
-@pytest.mark.parametrize("shape", SHAPES, ids=["fast", "generic"])
-def test_gradients_match_reference(shape):
+@pytest.mark.parametrize("shape,tc", SHAPES, ids=IDS)
+def test_gradients_match_reference(shape, tc):
     """BF16 operands, FP32 accumulation: the gradient vector within 3 % (relative L2)."""
-    sur, psi, target, C, L, dil = small_net(**shape)
+    sur, psi, target, C, L, dil = make(shape, tc)
     params = bf16_round(sur.params.cpu().numpy())
     loss_ref, g_ref = S.loss_and_grad(params, psi, target, C, L, dil)
     x = torch.as_tensor(psi, dtype=torch.complex64).cuda()
     t = torch.as_tensor(target, dtype=torch.complex64).cuda()
     g, loss = sur.gradients(x, t)
     g = g.cpu().numpy().astype(np.float64)
+    sur.sync()
     assert abs(loss - loss_ref) <= 2e-2 * loss_ref
     assert np.linalg.norm(g - g_ref) <= 3e-2 * np.linalg.norm(g_ref)
     # every layer's weight block individually
