@@ -475,13 +475,22 @@ def surrogate_form(args, dev):
         torch.cuda.synchronize(dev)
         out[f"rk4_ms_per_window_{dtype}"] = round(ev_time(lambda: g.step(win, dt), 10) * 1e3, 4)
         g.close()
+    # ---- RK4 windows of 8 states at once on separate streams (the parallel checker's cost) ----
+    from paper_1203_1263_gb300.surrogate import RK4Pool
+    pool = RK4Pool(n, 8, device=dev)
+    sts = [x[i] for i in range(8)]
+    pool.advance(sts)
+    torch.cuda.synchronize(dev)
+    out["rk4_ms_per_window_c128_8_streams"] = round(ev_time(lambda: pool.advance(sts), 5) / 8 * 1e3, 4)
+    pool.close()
+    out["infer_speedup_vs_rk4_c128_unchecked"] = round(out["rk4_ms_per_window_c128"] / out["infer_ms_per_window_batch16"], 2)
     # ---- budgeted training on FP64-integrator pairs, then rollouts ----
     t0 = time.perf_counter()
     X, Y, kept = generate_pairs(args.sur_traj, 125, n=n, seed=5, device=dev)
     t_gen = time.perf_counter() - t0
-    sur = Surrogate(n, n, channels=C, layers=nl, dilations=dil, max_batch=nb, seed=7)
+    sur = Surrogate(n, n, channels=C, layers=nl, dilations=dil, max_batch=32, seed=7)
     t0 = time.perf_counter()
-    hist = train(sur, X, Y, epochs=args.sur_epochs, batch=nb, lr=1e-3, lr_end=2e-5, seed=0)
+    hist = train(sur, X, Y, epochs=args.sur_epochs, batch=32, lr=5e-4, lr_end=1e-5, seed=0, noise=3e-3)
     torch.cuda.synchronize(dev)
     t_train_run = time.perf_counter() - t0
     del X, Y
@@ -491,15 +500,17 @@ def surrogate_form(args, dev):
         if k:
             psi0 = Xh[0].cpu().numpy().astype(np.complex128)
             break
-    out["training"] = {"pairs": int(kept * 125), "trajectories": kept, "epochs": args.sur_epochs,
+    out["training"] = {"pairs": int(kept * 125), "trajectories": kept, "epochs": args.sur_epochs, "batch": 32,
+                       "lr": "cosine 5e-4 -> 1e-5", "input_noise": 3e-3,
                        "loss_first_epoch": hist[0], "loss_last_epoch": hist[-1],
                        "data_seconds": round(t_gen, 2), "train_seconds": round(t_train_run, 2)}
     rollout(None, psi0, 2)                       # first calls load the kernels of the checks
     rollout(sur, psi0, 2, mode="strict")
+    rollout(sur, psi0, 2, mode="parallel", width=8)
     ref, st_plain = rollout(None, psi0, 125)
     rolls = {"plain_f64_seconds": round(st_plain.seconds, 4)}
-    for mode in ("strict", "sampled"):
-        got, st = rollout(sur, psi0, 125, mode=mode, every=4)
+    for mode in ("strict", "sampled", "parallel"):
+        got, st = rollout(sur, psi0, 125, mode=mode, every=4, width=8)
         err = float(torch.linalg.vector_norm(got - ref) / torch.linalg.vector_norm(ref))
         rolls[mode] = {"seconds": round(st.seconds, 4), "speedup_vs_f64": round(st_plain.seconds / st.seconds, 3),
                        "accepted_windows": st.accepted, "rk4_windows": st.rk4_windows, "checked": st.checked,
@@ -508,6 +519,7 @@ def surrogate_form(args, dev):
                        "median_check_rel_l2": float(np.median(st.l2_errors)) if st.l2_errors else None,
                        "final_rel_l2_vs_plain_f64": err}
     rolls["every"] = 4
+    rolls["parallel_width"] = 8
     rolls["tolerances"] = {"rel_l2": 1e-2, "mass_drift": 1e-4}
     out["rollout_t20"] = rolls
     sur.close()
@@ -531,8 +543,8 @@ def main():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--batch-runs", type=int, default=512)
     ap.add_argument("--no-surrogate", action="store_true")
-    ap.add_argument("--sur-traj", type=int, default=48, help="surrogate training trajectories (125 windows each)")
-    ap.add_argument("--sur-epochs", type=int, default=10)
+    ap.add_argument("--sur-traj", type=int, default=160, help="surrogate training trajectories (125 windows each)")
+    ap.add_argument("--sur-epochs", type=int, default=30)
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--ref-budget", type=float, default=90.0)
     args = ap.parse_args()

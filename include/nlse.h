@@ -214,7 +214,8 @@ int nlse_batch_destroy(nlse_batch_t b);
  * Learned surrogate (not in the paper): a residual 3x3-convolution network
  * that maps a 2D complex64 state psi(t) to psi(t + window), trained on states
  * the integrator itself produced.
- *   h_{-1} = (Re psi, Im psi);  z_l = conv3x3_{dil_l}(h_{l-1}) + b_l,  h_l = silu(z_l)
+ *   h_{-1} = (Re psi, Im psi, |psi|^2 Re psi, |psi|^2 Im psi)  (the cubic term as input features);
+ *   z_l = conv3x3_{dil_l}(h_{l-1}) + b_l,  h_l = silu(z_l)
  *   (l = 0 .. layers-2, `channels` channels);  y = conv3x3(h_{layers-2}) + b (2 channels);
  *   psi_out = psi_in + (y_0 + i y_1);  zero padding at the grid edges.
  * Activations are channels-last; every convolution (forward, backward-data,
@@ -256,8 +257,14 @@ int nlse_sur_forward(nlse_sur_t s, int nb, const void *psi_in, void *psi_out, in
 int nlse_sur_gradients(nlse_sur_t s, int nb, const void *psi_in, const void *psi_target, float *grad_out,
                        double *loss_out);
 
-/* One Adam step on a batch (forward, backward, update); *loss_out as above. */
-int nlse_sur_train_step(nlse_sur_t s, int nb, const void *psi_in, const void *psi_target, float lr,
+/* One Adam step on a batch (forward, backward, update); *loss_out as above.
+ * noise > 0 trains on psi_in + noise * max|psi_in| * (g + i g'), g and g'
+ * standard normal per site (drawn in the kernel from a counter-based
+ * SplitMix64 stream seeded by nlse_sur_init's seed and the step count), with
+ * the residual taken from that noisy input: the network learns to map
+ * slightly perturbed states, like its own predictions, onto the clean next
+ * window.  NLSE_EINVAL for lr <= 0 or noise < 0. */
+int nlse_sur_train_step(nlse_sur_t s, int nb, const void *psi_in, const void *psi_target, float lr, float noise,
                         double *loss_out);
 
 /* Convolution kernels: 1 (default) runs the forward and backward-data

@@ -3,7 +3,7 @@
 Only the tests may import it.  It writes out the network's definition
 directly with numpy, channels-last, zero padding:
 
-    h_{-1} = (Re psi, Im psi)
+    h_{-1} = (Re psi, Im psi, |psi|^2 Re psi, |psi|^2 Im psi)
     z_l[p, co] = b_l[co] + sum_{t, ci} W_l[co, t, ci] h_{l-1}[p + d_l o_t, ci]
     h_l = z_l * sigmoid(z_l)                       (l < L-1)
     psi_out = psi_in + z_{L-1}[.., 0] + i z_{L-1}[.., 1]
@@ -18,11 +18,13 @@ Parameter layout: per layer W [cout][9][cin] then b [cout].
 """
 import numpy as np
 
+N_IN = 4      # input features per pixel
+
 
 def layer_shapes(channels, layers):
     out = []
     for l in range(layers):
-        ci = 2 if l == 0 else channels
+        ci = N_IN if l == 0 else channels
         co = 2 if l == layers - 1 else channels
         out.append((co, ci))
     return out
@@ -60,7 +62,8 @@ def conv(x, Wl, bl, d):
 def forward(params, psi, channels, layers, dilations):
     """psi: complex [nb, H, W]; returns psi_out and the activations."""
     Ws, bs = unpack(params, channels, layers)
-    h = np.stack([psi.real, psi.imag], axis=-1).astype(np.float64)
+    r = np.abs(psi) ** 2
+    h = np.stack([psi.real, psi.imag, r * psi.real, r * psi.imag], axis=-1).astype(np.float64)
     hs, zs = [h], []
     for l in range(layers):
         z = conv(hs[-1], Ws[l], bs[l], dilations[l])

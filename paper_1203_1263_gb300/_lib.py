@@ -67,7 +67,7 @@ SIGNATURES = {
     "nlse_sur_sync_params": (_I, [_VP]),
     "nlse_sur_forward": (_I, [_VP, _I, _VP, _VP, _I]),
     "nlse_sur_gradients": (_I, [_VP, _I, _VP, _VP, _VP, ctypes.POINTER(_D)]),
-    "nlse_sur_train_step": (_I, [_VP, _I, _VP, _VP, ctypes.c_float, ctypes.POINTER(_D)]),
+    "nlse_sur_train_step": (_I, [_VP, _I, _VP, _VP, ctypes.c_float, ctypes.c_float, ctypes.POINTER(_D)]),
     "nlse_sur_set_kernel": (_I, [_VP, _I]),
     "nlse_sur_sync": (_I, [_VP]),
     "nlse_sur_destroy": (_I, [_VP]),

@@ -3,7 +3,7 @@
 // kernels in this file (BF16 tensor-core products with FP32 accumulation).
 //
 // Network (channels-last activations, H x W grid, batch nb):
-//   h_{-1} = (Re psi, Im psi)                                    2 channels
+//   h_{-1} = (Re psi, Im psi, |psi|^2 Re psi, |psi|^2 Im psi)    4 channels
 //   z_l = conv3x3_{dil_l}(h_{l-1}) + b_l,  h_l = silu(z_l)       l = 0 .. L-2, C channels
 //   y   = conv3x3_{dil_{L-1}}(h_{L-2}) + b_{L-1}                 2 channels
 //   psi_out = psi_in + (y_0 + i y_1)
@@ -1109,18 +1109,89 @@ __global__ void k_project(float2* __restrict__ out, int64_t HW, const double* __
 // exact zeros only.
 __host__ __device__ inline int pad_width(int C) { return (C % 16 == 0 && C <= 64) ? C : 16; }
 
-// complex state -> pc-channel BF16 input (Re, Im, zeros); one thread per 16-byte chunk
+// Input features per pixel: Re psi, Im psi, |psi|^2 Re psi, |psi|^2 Im psi
+// (the last two are the cubic term of the NLSE, so that one Euler step of
+// F(psi) is linear in the features).  Each feature x enters the first layer
+// as two BF16 channels, x_hi = bf16(x) and x_lo = bf16(x - x_hi), multiplied
+// by the same weight (the padded copy repeats W_0 for both), so the first
+// convolution sees the features at about 16 significant bits instead of 8.
+constexpr int kIn = 4;
+
+// complex state -> pc-channel BF16 input (the kIn features, zeros); one thread per 16-byte chunk
 __global__ void k_pack_input(const float2* __restrict__ psi, int64_t P, int pc, bf16* __restrict__ h) {
   const int cpp = pc / 8;
   uint4* dst = reinterpret_cast<uint4*>(h);
   for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < P * cpp; q += (int64_t)gridDim.x * blockDim.x) {
     uint4 v = make_uint4(0u, 0u, 0u, 0u);
-    if (q % cpp == 0) {
+    if (q % cpp == 0) {   // channels 0..3: hi parts, 4..7: lo parts of the kIn features
       const float2 z = psi[q / cpp];
-      const __nv_bfloat162 re_im = __floats2bfloat162_rn(z.x, z.y);
-      v.x = *reinterpret_cast<const uint32_t*>(&re_im);
+      const float r = fmaf(z.x, z.x, z.y * z.y);
+      const float f[4] = {z.x, z.y, r * z.x, r * z.y};
+      float hi[4], lo[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        hi[e] = __bfloat162float(__float2bfloat16_rn(f[e]));
+        lo[e] = f[e] - hi[e];
+      }
+      const __nv_bfloat162 a0 = __floats2bfloat162_rn(hi[0], hi[1]), a1 = __floats2bfloat162_rn(hi[2], hi[3]);
+      const __nv_bfloat162 b0 = __floats2bfloat162_rn(lo[0], lo[1]), b1 = __floats2bfloat162_rn(lo[2], lo[3]);
+      v.x = *reinterpret_cast<const uint32_t*>(&a0);
+      v.y = *reinterpret_cast<const uint32_t*>(&a1);
+      v.z = *reinterpret_cast<const uint32_t*>(&b0);
+      v.w = *reinterpret_cast<const uint32_t*>(&b1);
     }
     dst[q] = v;
+  }
+}
+
+// Per-state max |psi| partials: grid (kMassBlocks, nb), 256 threads -> part[n * kMassBlocks + block]
+__global__ void k_state_amax(const float2* __restrict__ psi, int64_t HW, float* __restrict__ part) {
+  __shared__ float r[256];
+  const int64_t base = (int64_t)blockIdx.y * HW;
+  float m = 0.f;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < HW; p += (int64_t)gridDim.x * blockDim.x) {
+    const float2 v = psi[base + p];
+    m = fmaxf(m, fmaf(v.x, v.x, v.y * v.y));
+  }
+  r[threadIdx.x] = m;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) r[threadIdx.x] = fmaxf(r[threadIdx.x], r[threadIdx.x + o]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[(int64_t)blockIdx.y * kMassBlocks + blockIdx.x] = sqrtf(r[0]);
+}
+
+__host__ __device__ __forceinline__ uint64_t splitmix64(uint64_t z) {
+  z += 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// Training input with noise: out = psi + sigma * max|psi_n| * (g_re + i g_im), g standard normal
+// (Box-Muller on two SplitMix64 uniforms per component, counter = seed-mixed element index).
+__global__ void k_add_noise(const float2* __restrict__ psi, int64_t HW, int nb, const float* __restrict__ amax_part,
+                            float sigma, uint64_t seed, float2* __restrict__ out) {
+  __shared__ float amp;
+  if (threadIdx.x == 0) {
+    float m = 0.f;
+    for (int i = 0; i < kMassBlocks; ++i) m = fmaxf(m, amax_part[(int64_t)blockIdx.y * kMassBlocks + i]);
+    amp = sigma * m;
+  }
+  __syncthreads();
+  const int64_t base = (int64_t)blockIdx.y * HW;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < HW; p += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t c = (uint64_t)(base + p) * 4u;
+    float g[2];
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      const float u1 = (float)((splitmix64(seed ^ (c + 2 * e)) >> 40) + 1) * (1.f / 16777217.f);   // (0, 1]
+      const float u2 = (float)(splitmix64(seed ^ (c + 2 * e + 1)) >> 40) * (1.f / 16777216.f);      // [0, 1)
+      g[e] = sqrtf(-2.f * logf(u1)) * cosf(6.283185307f * u2);
+    }
+    const float2 v = psi[base + p];
+    out[base + p] = make_float2(v.x + amp * g[0], v.y + amp * g[1]);
   }
 }
 
@@ -1185,7 +1256,7 @@ __global__ void k_bias_grad(const bf16* __restrict__ dz, int64_t P, int stride, 
 }
 
 // Padded operand copies of the end layers (BF16 weights from the BF16 copy, FP32 bias):
-//   w0[co][t][c]   = W_0[co][t][c] for c < 2, else 0            (C x 9 x pc)
+//   w0[co][t][c]   = W_0[co][t][c % kIn] for c < 2 kIn, else 0  (C x 9 x pc; hi and lo channels)
 //   wl[o][t][ci]   = W_{L-1}[o][t][ci] for o < 2, else 0        (pc x 9 x C)
 //   wlt[t][ci][o]  = the same, transposed for backward-data     (9 x C x pc)
 //   bl[o]          = b_{L-1}[o] for o < 2, else 0
@@ -1198,7 +1269,7 @@ __global__ void k_pad_ends(const bf16* __restrict__ w0src, const bf16* __restric
     {   // w0, i = (co * 9 + t) * pc + c
       const int c = int(i % pc);
       const int64_t ct = i / pc;
-      w0[i] = c < 2 ? w0src[ct * 2 + c] : zero;
+      w0[i] = c < 2 * kIn ? w0src[ct * kIn + (c % kIn)] : zero;
     }
     {   // wl, i = (o * 9 + t) * C + ci
       const int64_t o = i / (9 * (int64_t)C);
@@ -1215,14 +1286,15 @@ __global__ void k_pad_ends(const bf16* __restrict__ w0src, const bf16* __restric
 }
 
 // grad += the real part of a padded layer's gradient (scratch: weights, then pc bias slots):
-//   first layer: W[(co * 9 + t) * 2 + c] += scr[(co * 9 + t) * pc + c] (c < 2); b[co] += scr[nw + co], co < C
+//   first layer: W[(co * 9 + t) * kIn + c] += scr[.. * pc + c] + scr[.. * pc + kIn + c] (hi + lo); b[co] += scr[nw + co]
 //   last layer:  W[i] += scr[i] for i < 2 * 9 * C (rows 0, 1);             b[o] += scr[nw + o], o < 2
 __global__ void k_unpad_grad(const float* __restrict__ scr, float* __restrict__ dw, float* __restrict__ db, int C,
                              int pc, int first) {
-  const int64_t nw = (int64_t)C * 9 * pc, n = (int64_t)18 * C;
+  const int64_t nw = (int64_t)C * 9 * pc, n = (int64_t)9 * C * (first ? kIn : 2);
   const int nb = first ? C : 2;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n + nb; i += (int64_t)gridDim.x * blockDim.x) {
-    if (i < n) dw[i] += first ? scr[(i / 2) * pc + (i % 2)] : scr[i];
+    if (i < n)
+      dw[i] += first ? scr[(i / kIn) * pc + (i % kIn)] + scr[(i / kIn) * pc + kIn + (i % kIn)] : scr[i];
     else db[i - n] += scr[nw + (i - n)];
   }
 }
@@ -1280,6 +1352,9 @@ struct nlse_sur {
   float* m2;
   double* loss;
   double* mass_part;              // [max_batch][kMassBlocks][2]
+  float* amax_part;               // [max_batch][kMassBlocks]
+  float2* xnoisy;                 // noisy training input [max_batch][H][W]
+  uint64_t seed;
   int pc;                         // padded width of the two-channel ends
   bf16* hin;                      // input activation, pc channels (Re, Im, zeros)
   bf16* pw0;                      // padded first-layer weights [C][9][pc]
@@ -1301,13 +1376,13 @@ struct nlse_sur {
 
 namespace {
 
-int cin_of(const nlse_sur* s, int l) { return l == 0 ? 2 : s->C; }
+int cin_of(const nlse_sur* s, int l) { return l == 0 ? kIn : s->C; }
 int cout_of(const nlse_sur* s, int l) { return l == s->L - 1 ? 2 : s->C; }
 
 int64_t param_count(int C, int L) {
   int64_t n = 0;
   for (int l = 0; l < L; ++l) {
-    const int ci = l == 0 ? 2 : C, co = l == L - 1 ? 2 : C;
+    const int ci = l == 0 ? kIn : C, co = l == L - 1 ? 2 : C;
     n += (int64_t)co * 9 * ci + co;
   }
   return n;
@@ -1324,6 +1399,8 @@ size_t ws_bytes(int H, int W, int C, int L, int max_batch) {
   off = al(off + np * 4);            // m2
   off = al(off + 64);                // loss
   off = al(off + (size_t)max_batch * kMassBlocks * 2 * 8);   // mass_part
+  off = al(off + (size_t)max_batch * kMassBlocks * 4);       // amax_part
+  off = al(off + P * 8);                                      // xnoisy
   off = al(off + 16);                // err
   const int pc = pad_width(C);
   off = al(off + P * pc * 2);        // hin
@@ -1562,7 +1639,7 @@ cudaError_t backward(const nlse_sur* s, int nb, const float2* psi_in, const floa
     if (e != cudaSuccess) break;
     if (!bias_done) k_bias_grad<<<4 * s->num_sms, 256, 0, s->stream>>>(dz, P, o.cout, o.cout, o.db);
     if (first || last)
-      k_unpad_grad<<<grid1d((int64_t)18 * s->C + s->C), 256, 0, s->stream>>>(
+      k_unpad_grad<<<grid1d((int64_t)9 * kIn * s->C + s->C), 256, 0, s->stream>>>(
           s->wscr, s->grad + s->w_off[l], s->grad + s->b_off[l], s->C, s->pc, first ? 1 : 0);
     if ((e = cudaGetLastError()) != cudaSuccess) break;
     if (l > 0) {
@@ -1646,6 +1723,8 @@ int nlse_sur_create(nlse_sur_t* out, int H, int W, int channels, int layers, con
   s->m2 = (float*)(base + o); o = al(o + s->nparam * 4);
   s->loss = (double*)(base + o); o = al(o + 64);
   s->mass_part = (double*)(base + o); o = al(o + (size_t)max_batch * kMassBlocks * 2 * 8);
+  s->amax_part = (float*)(base + o); o = al(o + (size_t)max_batch * kMassBlocks * 4);
+  s->xnoisy = (float2*)(base + o); o = al(o + P * 8);
   s->err = (int*)(base + o); o = al(o + 16);
   s->pc = pad_width(channels);
   const int pc = s->pc;
@@ -1691,6 +1770,7 @@ int nlse_sur_create(nlse_sur_t* out, int H, int W, int channels, int layers, con
 
 int nlse_sur_init(nlse_sur_t s, uint64_t seed) {
   if (!s) return sfail(NLSE_EINVAL, "NULL surrogate");
+  s->seed = seed;
   for (int l = 0; l < s->L; ++l) {
     const int ci = cin_of(s, l), co = cout_of(s, l);
     // uniform He-style scale sqrt(6 / fan_in); the output layer starts small (near-identity residual)
@@ -1750,8 +1830,24 @@ int nlse_sur_gradients(nlse_sur_t s, int nb, const void* psi_in, const void* psi
   return e == cudaSuccess ? NLSE_OK : sfail(NLSE_ECUDA, cudaGetErrorString(e));
 }
 
-int nlse_sur_train_step(nlse_sur_t s, int nb, const void* psi_in, const void* psi_target, float lr, double* loss_out) {
-  int rc = nlse_sur_gradients(s, nb, psi_in, psi_target, nullptr, nullptr);
+int nlse_sur_train_step(nlse_sur_t s, int nb, const void* psi_in, const void* psi_target, float lr, float noise,
+                        double* loss_out) {
+  if (!s || !psi_in || !psi_target) return sfail(NLSE_EINVAL, "NULL argument");
+  if (nb < 1 || nb > s->max_batch) return sfail(NLSE_EINVAL, "batch outside 1..max_batch");
+  if (!(noise >= 0.f) || !(lr > 0.f)) return sfail(NLSE_EINVAL, "lr must be > 0 and noise >= 0");
+  const void* x = psi_in;
+  if (noise > 0.f) {
+    const int64_t HW = (int64_t)s->H * s->W;
+    const dim3 grid(kMassBlocks, (unsigned)nb);
+    k_state_amax<<<grid, 256, 0, s->stream>>>((const float2*)psi_in, HW, s->amax_part);
+    k_add_noise<<<grid, 256, 0, s->stream>>>((const float2*)psi_in, HW, nb, s->amax_part, noise,
+                                             splitmix64(s->seed ^ (0x5851F42D4C957F2Dull * (uint64_t)(s->adam_t + 1))),
+                                             s->xnoisy);
+    const cudaError_t e0 = cudaGetLastError();
+    if (e0 != cudaSuccess) return sfail(NLSE_ECUDA, cudaGetErrorString(e0));
+    x = s->xnoisy;
+  }
+  int rc = nlse_sur_gradients(s, nb, x, psi_target, nullptr, nullptr);
   if (rc != NLSE_OK) return rc;
   s->adam_t += 1;
   const float b1 = 0.9f, b2 = 0.999f;

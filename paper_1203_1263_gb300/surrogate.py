@@ -54,7 +54,7 @@ class Surrogate:
     def _layer_flops(self):
         out = []
         for l in range(self.L):
-            ci = 2 if l == 0 else self.C
+            ci = 4 if l == 0 else self.C
             co = 2 if l == self.L - 1 else self.C
             out.append(2.0 * self.H * self.W * 9 * ci * co)
         return out
@@ -99,12 +99,14 @@ class Surrogate:
                                              grad.data_ptr(), ctypes.byref(loss)))
         return grad, loss.value
 
-    def train_step(self, psi: torch.Tensor, target: torch.Tensor, lr: float, want_loss: bool = True):
-        """One Adam step on the batch (psi, target); returns the loss before the step."""
+    def train_step(self, psi: torch.Tensor, target: torch.Tensor, lr: float, want_loss: bool = True,
+                   noise: float = 0.0):
+        """One Adam step on the batch (psi, target); returns the loss before the
+        step.  noise: relative input noise (see nlse_sur_train_step)."""
         psi, target = self._pair(psi, target)
         loss = ctypes.c_double()
         L.check(self.lib.nlse_sur_train_step(self.s, psi.shape[0], psi.data_ptr(), target.data_ptr(), float(lr),
-                                             ctypes.byref(loss) if want_loss else None))
+                                             float(noise), ctypes.byref(loss) if want_loss else None))
         return loss.value if want_loss else None
 
     def set_kernel(self, tensor_core_gen: int) -> None:
@@ -132,40 +134,84 @@ class Surrogate:
 FOCUSING = dict(a=1.0, s=1.0, h=0.2, dt=0.005, window=32)
 
 
+class RK4Pool:
+    """`width` FP64 integrators of one n x n focusing problem, each on its own
+    CUDA stream, so that independent windows of RK4 run concurrently."""
+
+    def __init__(self, n: int, width: int, params=FOCUSING, device=None):
+        self.device = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+        self.params = params
+        zero = np.zeros((n, n), dtype=np.complex128)
+        self.streams = [torch.cuda.Stream(self.device) for _ in range(width)]
+        self.gs = [Integrator(zero, params["h"], params["a"], params["s"], None, "dirichlet", 4, "c128",
+                              device=self.device, stream=st) for st in self.streams]
+
+    def advance(self, starts, windows: int = 1):
+        """RK4 from each state in `starts` (complex64 [n, n] tensors, at most
+        `width`) by `windows` windows, concurrently; returns the complex64
+        results, ordered after the current stream."""
+        cur = torch.cuda.current_stream(self.device)
+        outs = []
+        for g, st, x in zip(self.gs, self.streams, starts):
+            st.wait_stream(cur)
+            with torch.cuda.stream(st):
+                g.psi.copy_(x)
+                g.step(self.params["window"] * windows, self.params["dt"])
+                outs.append(g.psi.to(torch.complex64))
+        for st in self.streams[:len(starts)]:
+            cur.wait_stream(st)
+        for o, st in zip(outs, self.streams):
+            o.record_stream(cur)
+        return outs
+
+    def close(self):
+        for g in self.gs:
+            g.close()
+
+
 def generate_pairs(n_traj: int, windows: int, n: int = 256, seed: int = 5, device=None, params=FOCUSING,
-                   blowup: float = 10.0):
+                   blowup: float = 10.0, concurrent: int = 16):
     """(psi_t, psi_{t+window}) pairs, complex64 [N, n, n], from FP64 RK4 runs of
-    the focusing 2D NLSE with Dirichlet walls, 2SHOC.  Initial states: 1-4
-    Gaussian humps (workloads.humps_2d).  Trajectories whose max|psi| exceeds
-    `blowup` x its initial value (collapse) are dropped."""
+    the focusing 2D NLSE with Dirichlet walls, 2SHOC, `concurrent` trajectories
+    at a time on separate streams.  Initial states: 1-4 Gaussian humps
+    (workloads.humps_2d).  Trajectories whose max|psi| exceeds `blowup` x its
+    initial value (collapse) are dropped.  Returns (X, Y, trajectories kept)."""
     dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
     X, Y = [], []
     kept = 0
-    for k in range(n_traj):
-        psi0 = W.humps_2d(seed, k, n=n, h=params["h"])
-        g = Integrator(psi0, params["h"], params["a"], params["s"], None, "dirichlet", 4, "c128", device=dev)
-        amp0 = float(np.max(np.abs(psi0)))
-        states = [g.psi.to(torch.complex64).clone()]
-        ok = True
-        for _ in range(windows):
-            g.step(params["window"], params["dt"])
-            states.append(g.psi.to(torch.complex64).clone())
+    width = max(1, min(concurrent, n_traj))
+    pool = RK4Pool(n, width, params, dev)
+    cur = torch.cuda.current_stream(dev)
+    for k0 in range(0, n_traj, width):
+        ks = list(range(k0, min(k0 + width, n_traj)))
+        psi0 = [W.humps_2d(seed, k, n=n, h=params["h"]) for k in ks]
+        snaps = [[] for _ in ks]
+        for g, st, p0, sn in zip(pool.gs, pool.streams, psi0, snaps):
+            st.wait_stream(cur)
+            with torch.cuda.stream(st):      # one FP64 trajectory per stream, snapshots in complex64
+                g.psi.copy_(torch.as_tensor(p0, dtype=torch.complex128).to(dev, non_blocking=False))
+                sn.append(g.psi.to(torch.complex64))
+                for _ in range(windows):
+                    g.step(params["window"], params["dt"])
+                    sn.append(g.psi.to(torch.complex64))
         torch.cuda.synchronize(dev)
-        if float(states[-1].abs().max()) > blowup * amp0 or not torch.isfinite(torch.view_as_real(states[-1])).all():
-            ok = False
-        g.close()
-        if not ok:
-            continue
-        kept += 1
-        X.extend(states[:-1])
-        Y.extend(states[1:])
+        for p0, sn in zip(psi0, snaps):
+            amp0 = float(np.max(np.abs(p0)))
+            last = sn[-1]
+            if float(last.abs().max()) > blowup * amp0 or not torch.isfinite(torch.view_as_real(last)).all():
+                continue
+            kept += 1
+            X.extend(sn[:-1])
+            Y.extend(sn[1:])
+    pool.close()
     return torch.stack(X), torch.stack(Y), kept
 
 
 def train(sur: Surrogate, X: torch.Tensor, Y: torch.Tensor, epochs: int, batch: int, lr: float, seed: int = 0,
-          log_every: int = 0, lr_end: Optional[float] = None):
+          log_every: int = 0, lr_end: Optional[float] = None, noise: float = 0.0):
     """Adam on shuffled mini-batches; returns the per-epoch mean loss.  With
-    lr_end the rate follows a cosine from lr down to lr_end over the run."""
+    lr_end the rate follows a cosine from lr down to lr_end over the run;
+    noise is the relative input noise of each step."""
     rng = np.random.default_rng(seed)
     hist = []
     per_epoch = max(1, X.shape[0] // batch)
@@ -179,7 +225,7 @@ def train(sur: Surrogate, X: torch.Tensor, Y: torch.Tensor, epochs: int, batch: 
             xb, yb = X[idx].contiguous(), Y[idx].contiguous()
             rate = lr if lr_end is None else lr_end + 0.5 * (lr - lr_end) * (1 + math.cos(math.pi * it / total))
             it += 1
-            loss = sur.train_step(xb, yb, rate, want_loss=(i // batch) % 8 == 0)
+            loss = sur.train_step(xb, yb, rate, want_loss=(i // batch) % 8 == 0, noise=noise)
             if loss is not None:
                 tot += loss
                 cnt += 1
@@ -214,7 +260,7 @@ def _mass(psi: torch.Tensor, h: float, out: torch.Tensor) -> float:
 
 
 def rollout(sur: Optional[Surrogate], psi0, n_windows: int, params=FOCUSING, mode: str = "strict", every: int = 4,
-            tol_l2: float = 1e-2, tol_mass: float = 1e-4, project: bool = True, device=None):
+            tol_l2: float = 1e-2, tol_mass: float = 1e-4, project: bool = True, device=None, width: int = 16):
     """Advance psi0 by n_windows windows of `window` RK4 steps.
 
     sur=None: plain FP64 RK4.  With a surrogate the rollout moves in spans of
@@ -227,9 +273,19 @@ def rollout(sur: Optional[Surrogate], psi0, n_windows: int, params=FOCUSING, mod
     from the same starting state and must agree within tol_l2 (relative L2).
     If either check fails the rollout returns to the span's verified starting
     state and advances the whole span with RK4.  States pass between windows
-    as complex64."""
-    if mode not in ("strict", "sampled"):
-        raise ValueError("mode must be 'strict' or 'sampled'")
+    as complex64.
+
+    "parallel" checks every window like "strict", but speculatively: the
+    network predicts up to `width` windows ahead, an RK4Pool re-runs all of
+    them at once (window j from predicted state j - 1, each on its own
+    stream), the longest prefix that passes both checks is accepted, and at
+    the first failing window the RK4 result from its (accepted) starting
+    state takes over.  The depth adapts: twice the last round's progress
+    after a failure, doubled after a clean round, between 2 and `width`."""
+    if mode not in ("strict", "sampled", "parallel"):
+        raise ValueError("mode must be 'strict', 'sampled' or 'parallel'")
+    if mode == "parallel":
+        return _rollout_parallel(sur, psi0, n_windows, params, width, tol_l2, tol_mass, project, device)
     dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
     h, dt, steps = params["h"], params["dt"], params["window"]
     g = Integrator(np.asarray(psi0), h, params["a"], params["s"], None, "dirichlet", 4, "c128", device=dev)
@@ -286,4 +342,60 @@ def rollout(sur: Optional[Surrogate], psi0, n_windows: int, params=FOCUSING, mod
     torch.cuda.synchronize(dev)
     st.seconds = time.perf_counter() - t0
     g.close()
+    return verified[0], st
+
+
+def _rollout_parallel(sur, psi0, n_windows, params, width, tol_l2, tol_mass, project, device):
+    dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+    h = params["h"]
+    n = int(np.asarray(psi0).shape[0])
+    pool = RK4Pool(n, width, params, dev)
+    lib = L.lib()
+    nn = L.int64_array((n, n))
+    st = RolloutStats()
+    masses = torch.zeros(width + 1, dtype=torch.float64, device=dev)
+    verified = torch.as_tensor(np.asarray(psi0), dtype=torch.complex64, device=dev)[None].contiguous()
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    w = 0
+    span = max(2, width // 4)         # speculation depth: doubled after a clean round, cut after a failure
+    while w < n_windows:
+        K = min(span, n_windows - w)
+        cur = torch.cuda.current_stream(dev)
+        preds = [verified]
+        for _ in range(K):
+            preds.append(sur.forward(preds[-1], project=project))
+        for j in range(K + 1):      # masses of the chain, one readback for the round
+            L.check(lib.nlse_mass_noalloc(2, nn, float(h), L.C64, preds[j].data_ptr(),
+                                          masses[j:j + 1].data_ptr(), cur.cuda_stream))
+        refs = pool.advance([p[0] for p in preds[:K]])
+        P = torch.cat(preds[1:])
+        R = torch.stack(refs)
+        errs = (torch.linalg.vector_norm(P - R, dim=(1, 2)) / torch.linalg.vector_norm(R, dim=(1, 2))).cpu().numpy()
+        m = masses[:K + 1].cpu().numpy()
+        drift = np.abs(m[1:] - m[:-1]) / m[:-1]
+        st.checked += K
+        st.l2_errors.extend(float(e) for e in errs)
+        st.max_mass_drift = max(st.max_mass_drift, float(np.max(drift)))
+        bad = np.nonzero(~((errs <= tol_l2) & (drift <= tol_mass)))[0]
+        if bad.size == 0:
+            st.accepted += K
+            verified = preds[K]
+            w += K
+            span = min(width, 2 * span)
+        else:
+            j = int(bad[0])                  # windows 0..j-1 of this round accepted, window j from RK4
+            span = max(2, min(width, 2 * (j + 1)))
+            st.accepted += j
+            st.rk4_windows += 1
+            if drift[j] > tol_mass or not np.isfinite(drift[j]):
+                st.rejected_mass += 1
+            else:
+                st.rejected_l2 += 1
+            verified = refs[j][None].contiguous()
+            w += j + 1
+        st.windows = w
+    torch.cuda.synchronize(dev)
+    st.seconds = time.perf_counter() - t0
+    pool.close()
     return verified[0], st
