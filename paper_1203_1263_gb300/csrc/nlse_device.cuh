@@ -376,6 +376,8 @@ struct StageArgs {
   double dt6;                  // dt/6 in FP64 (PMix stage 4)
   int stage;                   // 0 = write F only, 1..4 = RK4 stage
   unsigned int* flag;          // bit 0: non-finite Psi
+  int xwall;                   // 3D tiled path: the shell also owns x in [2, 1 + xwall] and its mirror
+                               // (deep-interior kernels start at x = 2 + xwall); 0 by default
 };
 
 // float <-> double on the integer pipe (GB300 issues FP64-pipe instructions,

@@ -5,6 +5,7 @@
 // many kernel instantiations compile in parallel.
 #pragma once
 #include "stage_generic.cuh"
+#include "stage_slab.cuh"
 #include "stage_tiled.cuh"
 #include "stage_tma.cuh"
 
@@ -19,16 +20,26 @@ cudaError_t launch_stage(const StageArgs<T>& A, const LaunchCfg& L, cudaStream_t
     if constexpr (fp64) if (exact) return launch_generic<T, D, ORDER, true>(A, stream);
     return launch_generic<T, D, ORDER>(A, stream);
   }
-  // tiled: deep interior (TMA-fed when the layout allows) + the wall shell
+  // tiled: deep interior (TMA-fed when the layout allows) + the wall shell, as
+  // shared-memory slabs (FP32 stages: three x layers per x wall) or, for thin
+  // grids, the global-memory shell kernel
+  const bool slabs = slab_ok(A.f.n);
+  constexpr int nsx = fp64 ? 1 : 3;   // x-wall layers owned by the slab shell
+  StageArgs<T> B = A;
+  B.xwall = slabs ? nsx - 1 : 0;
   auto deep = [&](cudaStream_t st) -> cudaError_t {
     if constexpr (fp64) {
-      if (exact) return L.tmap ? launch3d_tma<T, ORDER, true>(A, L, st) : launch3d_tiled<T, ORDER, true>(A, L.tile_cfg, st);
+      if (exact) return L.tmap ? launch3d_tma<T, ORDER, true>(B, L, st) : launch3d_tiled<T, ORDER, true>(B, L.tile_cfg, st);
     }
-    return L.tmap ? launch3d_tma<T, ORDER, false>(A, L, st) : launch3d_tiled<T, ORDER>(A, L.tile_cfg, st);
+    return L.tmap ? launch3d_tma<T, ORDER, false>(B, L, st) : launch3d_tiled<T, ORDER>(B, L.tile_cfg, st);
   };
   auto shell = [&](cudaStream_t st) -> cudaError_t {
-    if constexpr (fp64) if (exact) return launch_shell<T, D, ORDER, true>(A, st);
-    return launch_shell<T, D, ORDER>(A, st);
+    if (slabs) {
+      if constexpr (fp64) if (exact) return launch_shell_slabs<T, ORDER, true, nsx>(B, st);
+      return launch_shell_slabs<T, ORDER, false, nsx>(B, st);
+    }
+    if constexpr (fp64) if (exact) return launch_shell<T, D, ORDER, true>(B, st);
+    return launch_shell<T, D, ORDER>(B, st);
   };
   return launch_deep_and_shell(L, stream, has_deep(D, A.f.m), deep, shell);
 }

@@ -130,7 +130,7 @@ __global__ void __launch_bounds__(TX* TY) k_stage3d_tiled(const StageArgs<T> A, 
   __syncthreads();
 
   const int gx = x0 + threadIdx.x, gy = y0 + threadIdx.y;
-  const bool deep_xy = gx >= 2 && gx <= nx - 3 && gy >= 2 && gy <= ny - 3;   // wall shell: shell kernel
+  const bool deep_xy = gx >= 2 + A.xwall && gx <= nx - 3 - A.xwall && gy >= 2 && gy <= ny - 3;   // wall shell: shell kernel
   const int o = (threadIdx.y + 2) * W + threadIdx.x + 2;
   for (int z = zb; z < ze; ++z) {
     if (deep_xy && z >= 2 && z <= nz - 3) {

@@ -130,7 +130,8 @@ __global__ void __launch_bounds__(TX* TYT) k_stage3d_tma(const StageArgs<T> A, c
   for (int r = 0; r < RY; ++r) {
     gy[r] = y0 + threadIdx.y + r * TYT;
     o[r] = (threadIdx.y + r * TYT + 2) * G::W + threadIdx.x + 2;
-    deep[r] = gx >= 2 && gx <= nx - 3 && gy[r] >= 2 && gy[r] <= ny - 3;   // x, y at least 2 from the walls
+    // x, y at least 2 from the walls (x at least 2 + xwall when the slab shell owns more x layers)
+    deep[r] = gx >= 2 + A.xwall && gx <= nx - 3 - A.xwall && gy[r] >= 2 && gy[r] <= ny - 3;
     col[r] = (int64_t)gy[r] * nx + gx;
   }
 
@@ -286,7 +287,7 @@ __global__ void __launch_bounds__(TX* TYT) k_stage3d_tma_exact(const StageArgs<T
   for (int r = 0; r < RY; ++r) {
     gy[r] = y0 + threadIdx.y + r * TYT;
     o[r] = (threadIdx.y + r * TYT + 2) * G::W + threadIdx.x + 2;
-    deep[r] = gx >= 2 && gx <= nx - 3 && gy[r] >= 2 && gy[r] <= ny - 3;
+    deep[r] = gx >= 2 + A.xwall && gx <= nx - 3 - A.xwall && gy[r] >= 2 && gy[r] <= ny - 3;
     col[r] = (int64_t)gy[r] * nx + gx;
   }
 
