@@ -9,7 +9,7 @@
 // and the deep-interior kernels then start at x = 4 (StageArgs::xwall = 2).
 // The wider x-wall slab owns every site of the 32-byte rows x = 0..3 (and
 // their mirror), so the pointwise arrays of those rows are fetched by one
-// kernel only, and its threads for x = 1, 2, 3 of a row are adjacent lanes.
+// kernel only.
 // (The FP64 path keeps one x layer: there the deep kernel's exact-sum stencil
 // is cheaper per site than the slab's, and the FP64 pipe, not DRAM, bounds it.)
 // A CTA owns TF consecutive fast coordinates of one wall and MC consecutive
@@ -96,6 +96,8 @@ __global__ void __launch_bounds__(SlabShape<NS>::THREADS) k_stage_slab(const Sta
     win[pl * PL + nw * WF + fw] = v;
   }
   __syncthreads();
+  // tn fastest: the x-wall layers of one row are adjacent lanes (their pointwise
+  // operands share 32-byte sectors)
   const int tn = tid % NS, tf = (tid / NS) % kSlabTF, tm = tid / (NS * kSlabTF);
   const int fs = f0 + tf, ms = m0 + tm, ns = n_first + tn;
   if (fs > rg.f_hi || ms > rg.m_hi) return;
