@@ -124,10 +124,14 @@ struct nlse_ctx {
 namespace {
 
 // Tile shape in use: the caller's choice, else the measured default per form
-// (32x8 for FP64, 32x16 for the FP32 forms; nlse_autotune can refine it).
+// and size (nlse_autotune can refine it): 32x8 for FP64; for the FP32 forms
+// in 3D, 64x8 on planes of at least 256 x 256 sites (fewer, wider TMA boxes)
+// and 32x8 on smaller planes (enough CTAs to fill the SMs); 32x16 in 2D.
 int resolved_tile(const nlse_ctx* c) {
   if (c->tile_cfg >= 0) return c->tile_cfg;
-  return c->dtype == NLSE_C128 ? 0 : 2;
+  if (c->dtype == NLSE_C128) return 0;
+  if (c->d == 3) return c->n[1] * c->n[2] >= 256 * 256 ? 3 : 0;
+  return 2;
 }
 
 template <class T>
