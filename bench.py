@@ -478,6 +478,8 @@ def surrogate_form(args, dev):
         torch.cuda.synchronize(dev)
         out[f"rk4_ms_per_window_{dtype}"] = round(ev_time(lambda: g.step(win, dt), 10) * 1e3, 4)
         g.close()
+    if args.surrogate_kernels_only:
+        return out
     # ---- RK4 windows of 8 states at once on separate streams (the parallel checker's cost) ----
     from paper_1203_1263_gb300.surrogate import RK4Pool
     pool = RK4Pool(n, 8, device=dev)
@@ -548,6 +550,8 @@ def main():
     ap.add_argument("--no-surrogate", action="store_true")
     ap.add_argument("--sur-traj", type=int, default=160, help="surrogate training trajectories (125 windows each)")
     ap.add_argument("--sur-epochs", type=int, default=30)
+    ap.add_argument("--surrogate-kernels-only", action="store_true",
+                    help="print only the surrogate's kernel throughput (training and inference steps) and exit")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--ref-budget", type=float, default=90.0)
     args = ap.parse_args()
@@ -556,7 +560,12 @@ def main():
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
     local_rank = int(os.environ.get("LOCAL_RANK", 0))
-    if args.impl == "reference":
+    if args.surrogate_kernels_only:
+        import torch
+        dev = torch.device("cuda", local_rank)
+        torch.cuda.set_device(dev)
+        res = {"surrogate_kernels": surrogate_form(args, dev)} if rank == 0 else None
+    elif args.impl == "reference":
         res = run_reference(args, rank, world)
     else:
         res = run_ours(args, rank, world, local_rank)
