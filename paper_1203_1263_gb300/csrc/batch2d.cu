@@ -60,6 +60,13 @@ __device__ __forceinline__ void batch_tile(const StageArgs<P32>& A, int tx, int 
   const int ny = f.n[0], nx = f.n[1];
   const int tid = threadIdx.y * TX + threadIdx.x;
   const int x0 = tx * TX, y0 = ty * TY;
+  const int gx = x0 + threadIdx.x, gy = y0 + threadIdx.y;
+  const bool deep = gx >= 2 && gx <= nx - 3 && gy >= 2 && gy <= ny - 3;
+  const int64_t c = (int64_t)gy * nx + gx;
+  // the site's pointwise operands are requested first, so that their latency
+  // overlaps the tile's
+  PointVals<P32> pv;
+  if (deep) pv = load_point<P32>(A, c, f.V != nullptr);
 #pragma unroll
   for (int i = 0; i < NPER; ++i) {
     const int e = tid + i * NT;
@@ -70,11 +77,8 @@ __device__ __forceinline__ void batch_tile(const StageArgs<P32>& A, int tx, int 
     }
   }
   __syncthreads();
-  const int gx = x0 + threadIdx.x, gy = y0 + threadIdx.y;
-  if (gx >= 2 && gx <= nx - 3 && gy >= 2 && gy <= ny - 3) {
+  if (deep) {
     const int idx[2] = {gy, gx};
-    const int64_t c = (int64_t)gy * nx + gx;
-    const PointVals<P32> pv = load_point<P32>(A, c, f.V != nullptr);
     SAcc2<P32> acc;
     acc.p = tile;
     acc.w = W;

@@ -176,22 +176,24 @@ __global__ void __launch_bounds__(TX* TY) k_stage2d_tiled(const StageArgs<T> A) 
   const int ny = f.n[0], nx = f.n[1];
   const int tid = threadIdx.y * TX + threadIdx.x;
   const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+  const int gx = x0 + threadIdx.x, gy = y0 + threadIdx.y;
+  const bool deep = gx >= 2 && gx <= nx - 3 && gy >= 2 && gy <= ny - 3;   // wall shell: shell kernel
+  const int64_t c = (int64_t)gy * nx + gx;
+  PointVals<T> pv;   // requested before the tile, so that both latencies overlap
+  if (deep) pv = load_point<T>(A, c, f.V != nullptr);
 #pragma unroll
   for (int i = 0; i < NPER; ++i) {
     const int e = tid + i * NT;
     if (e < PS) {
       const int r = e / W, q = e - r * W;
-      const int gy = y0 - 2 + r, gx = x0 - 2 + q;
-      tile[e] = ring_value<EXACT, C, E>((gy >= 0 && gy < ny && gx >= 0 && gx < nx) ? f.in[(int64_t)gy * nx + gx]
-                                                                                   : C{0, 0}, f.F);
+      const int ty_ = y0 - 2 + r, tx_ = x0 - 2 + q;
+      tile[e] = ring_value<EXACT, C, E>((ty_ >= 0 && ty_ < ny && tx_ >= 0 && tx_ < nx) ? f.in[(int64_t)ty_ * nx + tx_]
+                                                                                       : C{0, 0}, f.F);
     }
   }
   __syncthreads();
-  const int gx = x0 + threadIdx.x, gy = y0 + threadIdx.y;
-  if (gx >= 2 && gx <= nx - 3 && gy >= 2 && gy <= ny - 3) {   // wall shell: shell kernel
+  if (deep) {
     const int idx[2] = {gy, gx};
-    const int64_t c = (int64_t)gy * nx + gx;
-    const PointVals<T> pv = load_point<T>(A, c, f.V != nullptr);
     if constexpr (EXACT) {
       SAccX2<T, 2> acc(f, c);
       acc.p = tile;
