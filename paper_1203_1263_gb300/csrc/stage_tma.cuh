@@ -223,7 +223,7 @@ __global__ void __launch_bounds__(TX* TYT) k_stage3d_tma(const StageArgs<T> A, c
 // exact integers; i2d_rn turns them into FP64 on the integer pipe.
 // ---------------------------------------------------------------------------
 template <class T, int ORDER, int S, int TX, int TYT, int RY, int P>
-__global__ void __launch_bounds__(TX* TYT) k_stage3d_tma_exact(const StageArgs<T> A,
+__global__ void __launch_bounds__(TX* TYT, 3) k_stage3d_tma_exact(const StageArgs<T> A,
                                                               const __grid_constant__ CUtensorMap tm, int zc,
                                                               long long spin_limit, uint32_t extra_tx) {
   static_assert(std::is_same<typename T::R, double>::value, "FP64 only");
