@@ -410,6 +410,12 @@ __device__ __forceinline__ float d2f_rn(double v) {
   return __uint_as_float(sgn | (ef << 23) | mf);
 }
 
+// isfinite by the exponent bits (integer pipe; the FP64 pipe is GB300's scarcest unit)
+__device__ __forceinline__ bool finite_bits(double v) {
+  return (__double2hiint(v) & 0x7FF00000) != 0x7FF00000;
+}
+__device__ __forceinline__ bool finite_bits(float v) { return (__float_as_uint(v) & 0x7F800000u) != 0x7F800000u; }
+
 // The pointwise operands of one site's update, loaded ahead of use.
 template <class T>
 struct PointVals {
@@ -462,7 +468,7 @@ __device__ __forceinline__ void rk_apply(const StageArgs<T>& A, int64_t i, typen
         A.n32[i] = C{d2f_rn(q.x), d2f_rn(q.y)};
       }
       A.master[i] = q;
-      if (!(isfinite(q.x) && isfinite(q.y))) atomicOr(A.flag, 1u);
+      if (!(finite_bits(q.x) && finite_bits(q.y))) atomicOr(A.flag, 1u);
       break;
     }
   }
