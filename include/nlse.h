@@ -198,11 +198,14 @@ int nlse_batch_create(nlse_batch_t *out, int nruns, const nlse_run_desc *runs, v
 /* Advance every run by nsteps RK4 steps of its own dt; asynchronous. */
 int nlse_batch_step(nlse_batch_t b, int64_t nsteps);
 
-/* Tile shape of the batched deep kernel (as nlse_set_kernel's tile_cfg; -1 = 64x8). */
+/* Tile shape of the batched deep kernel (as nlse_set_kernel's tile_cfg; -1 = 32x8, the measured best on
+ * the 512-run workload). */
 int nlse_batch_set_tile(nlse_batch_t b, int tile_cfg);
 
-/* Autotuner: time the tile shapes on the batch's own runs (stages 1-2 only,
- * no run's Psi is written) and keep the fastest.  Synchronises the stream. */
+/* Autotuner: time stages 1-3 of every tile shape on the batch's own runs
+ * (three passes in alternating order, the first one untimed; none of these
+ * stages writes any run's Psi) and keep the fastest shape; *best_ms is its
+ * mean stage time.  Synchronises the stream. */
 int nlse_batch_autotune(nlse_batch_t b, int *best_tile_cfg, float *best_ms);
 
 /* Wait for the stream; NLSE_ENONFINITE if any run produced a NaN or Inf. */

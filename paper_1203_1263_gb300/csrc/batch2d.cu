@@ -124,7 +124,7 @@ struct BatchLayout {
   std::vector<size_t> field_off;   // per run: K_tot, Psi_tmp, Psi_out (3 x 8 B x sites)
 };
 
-void tile_dims(int tile_cfg, int* tx, int* ty) { tma_tile_shape(tile_cfg < 0 ? 3 : tile_cfg, tx, ty); }
+void tile_dims(int tile_cfg, int* tx, int* ty) { tma_tile_shape(tile_cfg < 0 ? 0 : tile_cfg, tx, ty); }
 
 bool layout_batch(int nruns, const nlse_run_desc* runs, int tile_cfg, BatchLayout* L) {
   int tx, ty;
@@ -195,7 +195,7 @@ cudaError_t launch_batch_stage(const nlse_batch* b, int stage, cudaStream_t st) 
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   if ((e = cudaEventRecord(b->ev_join, b->side)) != cudaSuccess) return e;
-  switch (b->tile_cfg < 0 ? 3 : b->tile_cfg) {
+  switch (b->tile_cfg < 0 ? 0 : b->tile_cfg) {
     case 0: e = launch_deep<32, 8>(b, stage, st); break;
     case 1: e = launch_deep<64, 4>(b, stage, st); break;
     case 2: e = launch_deep<32, 16>(b, stage, st); break;
@@ -408,30 +408,35 @@ int nlse_batch_autotune(nlse_batch_t b, int* best_tile_cfg, float* best_ms) {
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  float best = 1e30f;
-  int cfg = -1;
+  float t_min[4] = {1e30f, 1e30f, 1e30f, 1e30f};
   int rc = NLSE_OK;
-  // time stage 2 (stage 1 first fills its inputs); neither stage writes any run's Psi
-  for (int t = 0; t < 4 && rc == NLSE_OK; ++t) {
-    rc = nlse_batch_set_tile(b, t);
-    if (rc != NLSE_OK) break;
-    cudaError_t e = launch_batch_stage(b, 1, b->stream);
-    if (e == cudaSuccess) e = launch_batch_stage(b, 2, b->stream);
-    if (e == cudaSuccess) e = cudaEventRecord(e0, b->stream);
-    for (int r = 0; r < 3 && e == cudaSuccess; ++r) e = launch_batch_stage(b, 2, b->stream);
-    if (e == cudaSuccess) e = cudaEventRecord(e1, b->stream);
-    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-    float ms = 0.f;
-    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-    if (e != cudaSuccess) rc = bfail(NLSE_ECUDA, cudaGetErrorString(e));
-    else if (ms / 3 < best) { best = ms / 3; cfg = t; }
+  // time stages 1-3 (none of them writes any run's Psi) for every tile shape,
+  // twice in alternating order, after one untimed pass each; keep each shape's
+  // fastest pass
+  for (int pass = 0; pass < 3 && rc == NLSE_OK; ++pass) {
+    for (int k = 0; k < 4 && rc == NLSE_OK; ++k) {
+      const int t = (pass == 1) ? 3 - k : k;
+      rc = nlse_batch_set_tile(b, t);
+      if (rc != NLSE_OK) break;
+      cudaError_t e = cudaEventRecord(e0, b->stream);
+      for (int st = 1; st <= 3 && e == cudaSuccess; ++st) e = launch_batch_stage(b, st, b->stream);
+      if (e == cudaSuccess) e = cudaEventRecord(e1, b->stream);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      float ms = 0.f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      if (e != cudaSuccess) rc = bfail(NLSE_ECUDA, cudaGetErrorString(e));
+      else if (pass > 0 && ms < t_min[t]) t_min[t] = ms;   // pass 0 warms every shape up
+    }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (rc != NLSE_OK) return rc;
+  int cfg = 0;
+  for (int t = 1; t < 4; ++t)
+    if (t_min[t] < t_min[cfg]) cfg = t;
   rc = nlse_batch_set_tile(b, cfg);
   if (best_tile_cfg) *best_tile_cfg = cfg;
-  if (best_ms) *best_ms = best;
+  if (best_ms) *best_ms = t_min[cfg] / 3.f;
   return rc;
 }
 
