@@ -129,7 +129,7 @@ void tile_dims(int tile_cfg, int* tx, int* ty) { tma_tile_shape(tile_cfg < 0 ? 0
 bool layout_batch(int nruns, const nlse_run_desc* runs, int tile_cfg, BatchLayout* L) {
   int tx, ty;
   tile_dims(tile_cfg, &tx, &ty);
-  size_t off = 0;
+  size_t off = 256;   // bytes 0..255: the status word, at the same place for every tile shape
   auto al = [](size_t x) { return (x + 255) / 256 * 256; };
   L->runs_off = off;
   off = al(off + sizeof(BatchRun) * nruns);
@@ -154,7 +154,7 @@ bool layout_batch(int nruns, const nlse_run_desc* runs, int tile_cfg, BatchLayou
     L->field_off[r] = off;
     off = al(off + 3 * sizeof(float2) * size_t(runs[r].n[0] * runs[r].n[1]));
   }
-  L->total = al(off + 256);   // + status word
+  L->total = al(off);
   return true;
 }
 
@@ -169,7 +169,7 @@ struct nlse_batch {
   cudaEvent_t ev_fork, ev_join;
   cudaGraphExec_t exec;
   int tile_cfg;
-  unsigned int* flag() const { return (unsigned int*)(ws + lay.total - 256); }
+  unsigned int* flag() const { return (unsigned int*)ws; }   // fixed: the layout after it depends on the tile shape
 };
 
 namespace {
@@ -177,7 +177,19 @@ namespace {
 template <int TX, int TY>
 cudaError_t launch_deep(const nlse_batch* b, int stage, cudaStream_t st) {
   if (b->lay.ndeep == 0) return cudaSuccess;
-  int grid = 152 * 6;
+  // one wave of persistent CTAs: as many as fit on every SM at once for this tile shape
+  static int per_sm = 0, sms = 0;
+  if (per_sm == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch2d_deep<TX, TY>, TX * TY, 0) != cudaSuccess ||
+        per_sm < 1) {
+      cudaGetLastError();
+      per_sm = 1;
+    }
+  }
+  int grid = sms * per_sm;
   if (grid > b->lay.ndeep) grid = b->lay.ndeep;
   k_batch2d_deep<TX, TY><<<grid, dim3(TX, TY), 0, st>>>((const BatchRun*)(b->ws + b->lay.runs_off),
                                                          (const DeepItem*)(b->ws + b->lay.deep_off), b->lay.ndeep,

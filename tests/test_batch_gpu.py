@@ -88,3 +88,20 @@ def test_batch_rejects_bad_runs():
     runs[1] = dict(runs[1], order=3)
     with pytest.raises(L.NLSEError):
         BatchIntegrator(runs)
+
+
+def test_switching_tiles_on_one_batch_keeps_results():
+    """The work lists (and the run fields after them) move when the tile shape
+    changes; the status word must not, and every shape must continue the
+    same integration."""
+    runs = small_runs(seed=6, nruns=9)
+    ref = BatchIntegrator(runs)
+    ref.step(8)
+    ref.sync()
+    b = BatchIntegrator(runs)
+    for t in (1, 3, 0, 2):
+        b.set_tile(t)
+        b.step(2)
+        b.sync()
+    for i in range(len(runs)):
+        assert np.array_equal(b.numpy(i), ref.numpy(i)), i
