@@ -149,7 +149,7 @@ def test_split_continuation_and_determinism_bitwise(dtype, variant):
 
 @pytest.mark.parametrize("dtype", ["c128", "c64", "c64_acc64"])
 @pytest.mark.parametrize("dims,shape", [(2, (19, 45)), (3, (9, 21, 70)), (3, (20, 17, 64)), (3, (5, 40, 131)),
-                                        (3, (70, 36, 75))])
+                                        (3, (70, 36, 75)), (3, (7, 7, 10)), (3, (12, 9, 9))])
 @pytest.mark.parametrize("tile_cfg", [0, 1, 2, 3])
 def test_tiled_kernel_equals_generic_bitwise(dtype, dims, shape, tile_cfg):
     """The tiled kernels perform the generic kernel's arithmetic in the same
