@@ -499,34 +499,43 @@ def surrogate_form(args, dev):
     torch.cuda.synchronize(dev)
     t_train_run = time.perf_counter() - t0
     del X, Y
-    psi0 = None
-    for j in range(8):          # a held-out initial state whose trajectory does not collapse
+    held = []
+    for j in range(12):         # held-out initial states whose trajectories do not collapse
         Xh, _, k = generate_pairs(1, 125, n=n, seed=99 + j, device=dev)
         if k:
-            psi0 = Xh[0].cpu().numpy().astype(np.complex128)
+            held.append((99 + j, Xh[0].cpu().numpy().astype(np.complex128)))
+        if len(held) == 3:
             break
     out["training"] = {"pairs": int(kept * 125), "trajectories": kept, "epochs": args.sur_epochs, "batch": 32,
                        "lr": "cosine 5e-4 -> 1e-5", "input_noise": 3e-3,
                        "loss_first_epoch": hist[0], "loss_last_epoch": hist[-1],
                        "data_seconds": round(t_gen, 2), "train_seconds": round(t_train_run, 2)}
-    rollout(None, psi0, 2)                       # first calls load the kernels of the checks
-    rollout(sur, psi0, 2, mode="strict")
-    rollout(sur, psi0, 2, mode="parallel", width=8)
-    ref, st_plain = rollout(None, psi0, 125)
-    rolls = {"plain_f64_seconds": round(st_plain.seconds, 4)}
-    for mode in ("strict", "sampled", "parallel"):
-        got, st = rollout(sur, psi0, 125, mode=mode, every=4, width=8)
-        err = float(torch.linalg.vector_norm(got - ref) / torch.linalg.vector_norm(ref))
-        rolls[mode] = {"seconds": round(st.seconds, 4), "speedup_vs_f64": round(st_plain.seconds / st.seconds, 3),
-                       "accepted_windows": st.accepted, "rk4_windows": st.rk4_windows, "checked": st.checked,
-                       "rejected_l2": st.rejected_l2, "rejected_mass": st.rejected_mass,
-                       "max_mass_drift_per_window": st.max_mass_drift,
-                       "median_check_rel_l2": float(np.median(st.l2_errors)) if st.l2_errors else None,
-                       "final_rel_l2_vs_plain_f64": err}
-    rolls["every"] = 4
-    rolls["parallel_width"] = 8
-    rolls["tolerances"] = {"rel_l2": 1e-2, "mass_drift": 1e-4}
-    out["rollout_t20"] = rolls
+    psi_w = held[0][1]
+    rollout(None, psi_w, 2)                      # first calls load the kernels of the checks
+    rollout(sur, psi_w, 2, mode="strict")
+    rollout(sur, psi_w, 2, mode="parallel", width=8)
+    per_state = []
+    for seed, psi0 in held:
+        ref, st_plain = rollout(None, psi0, 125)
+        rolls = {"seed": seed, "plain_f64_seconds": round(st_plain.seconds, 4)}
+        for mode in ("strict", "sampled", "parallel"):
+            got, st = rollout(sur, psi0, 125, mode=mode, every=4, width=8)
+            err = float(torch.linalg.vector_norm(got - ref) / torch.linalg.vector_norm(ref))
+            rolls[mode] = {"seconds": round(st.seconds, 4),
+                           "speedup_vs_f64": round(st_plain.seconds / st.seconds, 3),
+                           "accepted_windows": st.accepted, "rk4_windows": st.rk4_windows, "checked": st.checked,
+                           "rejected_l2": st.rejected_l2, "rejected_mass": st.rejected_mass,
+                           "max_mass_drift_per_window": st.max_mass_drift,
+                           "median_check_rel_l2": float(np.median(st.l2_errors)) if st.l2_errors else None,
+                           "final_rel_l2_vs_plain_f64": err}
+        per_state.append(rolls)
+    summary = {m: {"mean_speedup_vs_f64": round(float(np.mean([r[m]["speedup_vs_f64"] for r in per_state])), 3),
+                   "accepted_windows": [r[m]["accepted_windows"] for r in per_state],
+                   "max_final_rel_l2_vs_plain_f64": max(r[m]["final_rel_l2_vs_plain_f64"] for r in per_state)}
+               for m in ("strict", "sampled", "parallel")}
+    out["rollout_t20"] = {"windows": 125, "every": 4, "parallel_width": 8,
+                          "tolerances": {"rel_l2": 1e-2, "mass_drift": 1e-4},
+                          "summary": summary, "held_out": per_state}
     sur.close()
     return out
 
@@ -549,7 +558,7 @@ def main():
     ap.add_argument("--batch-runs", type=int, default=512)
     ap.add_argument("--no-surrogate", action="store_true")
     ap.add_argument("--sur-traj", type=int, default=160, help="surrogate training trajectories (125 windows each)")
-    ap.add_argument("--sur-epochs", type=int, default=30)
+    ap.add_argument("--sur-epochs", type=int, default=60)
     ap.add_argument("--surrogate-kernels-only", action="store_true",
                     help="print only the surrogate's kernel throughput (training and inference steps) and exit")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
