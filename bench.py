@@ -23,6 +23,7 @@ import os
 import platform
 import statistics
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -118,7 +119,9 @@ class ClockSampler:
     def __init__(self, gpu_index: int):
         self.gpu = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_gpu{gpu_index}.csv")
+        # the raw samples go to a temporary file, or to NLSE_CLOCKS_DIR when that is set
+        out_dir = os.environ.get("NLSE_CLOCKS_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(out_dir, f"nlse_clocks_gpu{gpu_index}_{os.getpid()}.csv")
 
     def start(self):
         try:
