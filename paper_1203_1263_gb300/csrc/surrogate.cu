@@ -9,12 +9,18 @@
 //   psi_out = psi_in + (y_0 + i y_1)
 // with zero padding at the grid edges.  Parameters are FP32 masters; the
 // products use BF16 copies.  Every convolution (forward, backward-data,
-// weight-gradient) is one implicit GEMM, C[M x N] += A[M x K] B[K x N], whose
-// A and B tiles are gathered from the activations and weights into shared
-// memory as BF16 and multiplied with mma.sync.m16n8k16 (FP32 accumulators):
+// weight-gradient) is an implicit GEMM, C[M x N] += A[M x K] B[K x N]:
 //   forward        M = pixels, N = Cout, K = 9 Cin: A[p,(t,ci)] = h[p + d o_t, ci], B[(t,ci),co] = W[co,t,ci]
 //   backward-data  M = pixels, N = Cin,  K = 9 Cout: A[p,(t,co)] = dz[p - d o_t, co], B[(t,co),ci] = W[co,t,ci]
 //   weight-grad    M = Cout,   N = 9 Cin, K = pixels: A[co,p] = dz[p, co], B[p,(t,ci)] = h[p + d o_t, ci]
+// Three kernel families compute them:
+//   - tcgen05 (k_conv_tc, k_wgrad_tc): TMA-fed halo tiles in shared memory,
+//     the nine taps as shifted descriptors over one tile, TMEM accumulators;
+//     used for every layer whose channel counts fit (the 64-channel network
+//     runs entirely on them);
+//   - mma.sync.m16n8k16 with cp.async / ldmatrix staging (k_conv_fast), for
+//     channel counts that are multiples of 8 (and for comparison);
+//   - a scalar-gather mma.sync kernel (k_conv) for any other shape.
 // Loss: mean squared error of psi_out against the target (Re and Im parts);
 // optimiser: Adam.
 #include <cuda.h>
