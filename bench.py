@@ -166,6 +166,21 @@ def build_problem(name):
     return W.trap_vortex_3d(shape=spec["shape"])
 
 
+def slowest_rank(seconds, device, dist=None):
+    """The job's time across replicas: the maximum of every rank's `seconds`
+    (each rank integrates its own replica; nothing else is exchanged)."""
+    import torch
+    t = torch.tensor([float(seconds)], dtype=torch.float64, device=device)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(site_steps_per_rank, seconds, device, world=1, dist=None):
+    """Whole-job Gsite-step/s: all ranks' site-steps over the slowest rank's time."""
+    return world * site_steps_per_rank / slowest_rank(seconds, device, dist) / 1e9
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     from paper_1203_1263_gb300.integrator import Integrator, max_dt
@@ -214,10 +229,7 @@ def run_ours(args, rank, world, local_rank):
 
     K, Wm = args.steps, args.warmup
     g64, ms, wall, clocks = timed(args.dtype, K, Wm)
-    t = torch.tensor([ms], dtype=torch.float64, device=dev)
-    if dist is not None:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
+    ms_max = slowest_rank(ms, dev, dist)
     value = world * sites * K / (ms_max * 1e-3) / 1e9
 
     result = None
@@ -289,11 +301,8 @@ def run_ours(args, rank, world, local_rank):
                 g.mass()          # synchronises the stream: the frame's result is on the host
             wall = time.perf_counter() - w0
             barrier()
-        t = torch.tensor([wall], dtype=torch.float64, device=dev)
-        if dist is not None:
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_v = job_throughput(sites * CHUNK * frames, wall, dev, world, dist)
         if rank == 0:
-            e2e_v = world * sites * CHUNK * frames / float(t.item()) / 1e9
             nbytes = host_in.numel() * host_in.element_size()
             result["e2e"] = {"value": round(e2e_v, 4), "unit": UNIT,
                              "h2d_bytes_per_step": nbytes // CHUNK, "d2h_bytes_per_step": (nbytes + 8) // CHUNK,
