@@ -760,14 +760,16 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_conv_tc(const TcArgs a, const
         if (k >= 1 && !role_wait(&acce_b[st], (k - 1) & 1, a.spin_limit, &abort_flag)) { aborted = true; break; }
         tc_fence_after();
         const uint32_t a0 = sm_base + BSZ + st * ASZ;
+#pragma unroll
         for (int t = 0; t < 9; ++t) {
           const int sy = sgn * tap_dy(t), sx = sgn * tap_dx(t);
           if (LAYOUT) {
-            const uint32_t aoff = a0 + (uint32_t)(((1 + sy) * RW + d + sx * d) * 128);
-            const uint32_t boff = sm_base + (uint32_t)(t * nout * 128);
+            // one descriptor per tap; the K slices step the 16-byte start-address field by 2 (32 bytes)
+            const uint64_t ad0 = sdesc_sw128(a0 + (uint32_t)(((1 + sy) * RW + d + sx * d) * 128));
+            const uint64_t bd0 = sdesc_sw128(sm_base + (uint32_t)(t * nout * 128));
+#pragma unroll
             for (int kk = 0; kk < 4; ++kk)
-              tc_mma(tmem + (uint32_t)(st * nout), sdesc_sw128(aoff + 32 * kk), sdesc_sw128(boff + 32 * kk), idesc,
-                     (t | kk) != 0);
+              tc_mma(tmem + (uint32_t)(st * nout), ad0 + 2u * kk, bd0 + 2u * kk, idesc, (t | kk) != 0);
           } else {
             const uint32_t aoff = a0 + (uint32_t)(((1 + sy) * RW + d + sx * d) * 16);
             const uint32_t boff = sm_base + (uint32_t)(t * planes * nout * 16);
@@ -989,14 +991,17 @@ __global__ void __launch_bounds__(kWgThreads, 1) k_wgrad_tc(const WgArgs a, cons
         }
         tc_fence_after();
         const uint32_t halo = base + st * STG, dzt = halo + HALO;
+#pragma unroll
         for (int pi = 0; pi < 5; ++pi) {
           const int t1 = 2 * pi, t2 = 2 * pi + 1;
           const uint32_t v1 = halo + (uint32_t)(((1 + tap_dy(t1)) * RW + d + tap_dx(t1) * d) * 128);
           const uint32_t v2 = pi < 4 ? halo + (uint32_t)(((1 + tap_dy(t2)) * RW + d + tap_dx(t2) * d) * 128)
                                      : base + 2 * STG;   // ones: the bias gradient
+          // K steps of 16 pixels move both starts by 2048 bytes: 128 in the 16-byte address field
+          const uint64_t ad0 = sdesc_sw128(v1, v2 - v1), bd0 = sdesc_sw128(dzt);
+#pragma unroll
           for (int kk = 0; kk < 8; ++kk)
-            tc_mma(tmem + (uint32_t)(pi * 64), sdesc_sw128(v1 + kk * 2048, v2 - v1), sdesc_sw128(dzt + kk * 2048),
-                   idesc, (i > 0 || kk > 0) ? 1u : 0u);
+            tc_mma(tmem + (uint32_t)(pi * 64), ad0 + 128u * kk, bd0 + 128u * kk, idesc, (i > 0 || kk > 0) ? 1u : 0u);
         }
         tc_commit(&empty_b[st]);
       }
