@@ -61,7 +61,7 @@ constexpr size_t kAlign = 256;
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 struct Layout {
-  size_t ktot, ptmp, pout, pn32, partials, status, total;
+  size_t ktot, ptmp, pout, pn32, vs, partials, status, total;
 };
 
 bool layout_for(int dims, const int64_t* N, int dtype, Layout* L, int64_t* total_sites) {
@@ -79,6 +79,7 @@ bool layout_for(int dims, const int64_t* N, int dtype, Layout* L, int64_t* total
   L->ptmp = off; off = align_up(off + es * total);
   L->pout = off; off = align_up(off + es * total);
   L->pn32 = off; if (dtype == NLSE_C64_ACC64) off = align_up(off + 8 * total);
+  L->vs = off; if (dtype == NLSE_C128) off = align_up(off + 8 * total);   // V / cLF for the exact-sum stages
   L->partials = off; off = align_up(off + sizeof(double) * 2 * kMaxReduceBlocks);
   L->status = off; off = align_up(off + 256);
   L->total = off;
@@ -157,6 +158,8 @@ Field<T> make_field(const nlse_ctx* c, const void* in) {
   f.bc = c->bc;
   f.F = c->fixF;
   f.cLF = ldexp(c->order == 4 ? c->a / (12.0 * c->h * c->h) : c->a / (c->h * c->h), -c->fixF);
+  f.invcLF = R(1.0 / f.cLF);
+  f.sG = R(c->s / f.cLF);
   f.V = (const typename T::VR*)c->V;
   f.in = (const typename T::C*)in;
   return f;
@@ -235,10 +238,13 @@ cudaError_t launch_one_stage(const nlse_ctx* c, int s, double dt, cudaStream_t s
   A.out = outs[i];
   A.master = (typename T::M*)c->psi;
   A.n32 = mix ? (C*)c->at(c->lay.pn32) : nullptr;
-  A.dtc = R(dtc[i]);
+  // FP64 with the exact-sum stencil: F is formed in units of cLF, so the stage coefficient carries it
+  const bool g = std::is_same<T, P64>::value && c->variant >= 2;
+  A.dtc = R(g ? dtc[i] * A.f.cLF : dtc[i]);
   A.dt6 = dt / 6.0;
   A.stage = s;
   A.flag = c->flag();
+  A.Vs = (g && c->V) ? (const typename T::VR*)c->at(c->lay.vs) : nullptr;
   return dispatch_stage<T>(c, A, stage_tmap(c, inbuf[i], in[i]), st);
 }
 
@@ -328,6 +334,18 @@ void record_last_error(const char* msg) { snprintf(g_err, sizeof(g_err), "%s", m
 
 // cuTensorMapEncodeTiled for other translation units (nullptr when unavailable).
 void* tensor_map_encoder() { return reinterpret_cast<void*>(encode_fn()); }
+
+__global__ void k_scale_v(const double* __restrict__ V, double s, int64_t n, double* __restrict__ Vs) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    Vs[i] = V[i] * s;
+}
+
+cudaError_t launch_scale_v(const double* V, double s, int64_t n, double* Vs, cudaStream_t stream) {
+  int64_t b = (n + 255) / 256;
+  if (b > 152 * 16) b = 152 * 16;
+  k_scale_v<<<(unsigned)b, 256, 0, stream>>>(V, s, n, Vs);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_round_master(const double2* master, float2* n32, int64_t total, cudaStream_t stream) {
   int64_t b = (total + 255) / 256;
@@ -419,6 +437,10 @@ int nlse_create(nlse_t* out, int dims, const int64_t* N, double h, double a, dou
       c->fixF = 54 - (ex + 3);
     }
   }
+  if (e == cudaSuccess && dtype == NLSE_C128 && V) {   // V / cLF for the exact-sum stages
+    const Field<P64> f = make_field<P64>(c, psi);
+    e = launch_scale_v((const double*)V, 1.0 / f.cLF, total, (double*)c->at(L.vs), c->stream);
+  }
   if (e != cudaSuccess) {
     nlse_destroy(c);
     return cuda_fail(e, "nlse_create");
@@ -475,6 +497,9 @@ int nlse_rhs(nlse_t c, const void* psi_in, void* F_out) {
     A.out = (typename T::C*)F_out;
     A.stage = 0;
     A.flag = c->flag();
+    const bool g = std::is_same<T, P64>::value && c->variant >= 2;   // F in units of cLF: scale it back
+    A.dtc = typename T::R(g ? A.f.cLF : 1.0);
+    A.Vs = (g && c->V) ? (const typename T::VR*)c->at(c->lay.vs) : nullptr;
     return dispatch_stage<T>(c, A, nullptr, c->stream);
   };
   if (c->dtype == NLSE_C128) e = run(P64{});

@@ -75,6 +75,8 @@ struct Field {
   int bc;
   int F;             // exact-sum stencil: fixed-point fraction bits
   double cLF;        // exact-sum stencil: cL * 2^-F
+  R sG;              // exact-sum stencil: s / cLF
+  R invcLF;          // exact-sum stencil: 1 / cLF
   const typename T::VR* V;
   const typename T::C* in;   // the field (stage input Psi)
 };
@@ -284,9 +286,12 @@ __device__ __forceinline__ double i2d_rn(long long v) {
   return __longlong_as_double((long long)(sgn | ((unsigned long long)(e + 1023) << 52) | (m & 0x000FFFFFFFFFFFFFull)));
 }
 
+// The exact-sum Laplacian in units of cLF = cL 2^-F (the exact integer sum
+// itself, rounded once to FP64); Ng = N_c / cLF.  Sites with an operand
+// outside the fixed-point range take the FP64 stencil, rescaled.
 template <class T, int D, int ORDER, class Acc>
 __device__ __forceinline__ double2 a_lap_exact(const Field<T>& f, const Acc& acc, const int* idx, int64_t c,
-                                               double2 pc, double Nc) {
+                                               double2 pc, double Ng) {
   static_assert(std::is_same<typename T::R, double>::value, "exact-sum stencil is FP64 only");
   const longlong2 cc = acc.fx0();
   bool bad = fbad(cc);
@@ -298,9 +303,13 @@ __device__ __forceinline__ double2 a_lap_exact(const Field<T>& f, const Acc& acc
     s1x += u.x + w.x;
     s1y += u.y + w.y;
   }
+  const double Nc = Ng * f.cLF;   // physical N_c, for the walls' ghosts and the fallback
   if constexpr (ORDER == 2) {
-    if (bad) return a_lap_slow<T, D, ORDER>(f, acc, idx, c, pc, Nc);
-    return {f.cLF * __ll2double_rn(s1x - 2 * D * cc.x), f.cLF * __ll2double_rn(s1y - 2 * D * cc.y)};
+    if (bad) {
+      const double2 aL = a_lap_slow<T, D, ORDER>(f, acc, idx, c, pc, Nc);
+      return {aL.x * f.invcLF, aL.y * f.invcLF};
+    }
+    return {i2d_rn(s1x - 2 * D * cc.x), i2d_rn(s1y - 2 * D * cc.y)};
   }
   const bool wall = near_wall2<D>(idx, f.n);
   long long s2x = 0, s2y = 0;
@@ -317,17 +326,20 @@ __device__ __forceinline__ double2 a_lap_exact(const Field<T>& f, const Acc& acc
     s2x = s2.x;
     s2y = s2.y;
   }
-  if (bad) return a_lap_slow<T, D, ORDER>(f, acc, idx, c, pc, Nc);
+  if (bad) {
+    const double2 aL = a_lap_slow<T, D, ORDER>(f, acc, idx, c, pc, Nc);
+    return {aL.x * f.invcLF, aL.y * f.invcLF};
+  }
   const long long Sx = 16 * s1x - s2x - 30 * D * cc.x;
   const long long Sy = 16 * s1y - s2y - 30 * D * cc.y;
-  return {f.cLF * __ll2double_rn(Sx), f.cLF * __ll2double_rn(Sy)};
+  return {i2d_rn(Sx), i2d_rn(Sy)};
 }
 
-// The exact-sum Laplacian at a deep-interior site (no wall within two cells):
-// the same integer sums as a_lap_exact without its wall branch.
+// The exact-sum Laplacian at a deep-interior site (no wall within two cells),
+// in units of cLF like a_lap_exact, without its wall branch.
 template <class T, int D, int ORDER, class Acc>
 __device__ __forceinline__ double2 a_lap_exact_deep(const Field<T>& f, const Acc& acc, const int* idx, int64_t c,
-                                                    double2 pc, double Nc) {
+                                                    double2 pc, double Ng) {
   const longlong2 cc = acc.fx0();
   bool bad = fbad(cc);
   long long s1x = 0, s1y = 0;
@@ -339,8 +351,11 @@ __device__ __forceinline__ double2 a_lap_exact_deep(const Field<T>& f, const Acc
     s1y += u.y + w.y;
   }
   if constexpr (ORDER == 2) {
-    if (bad) return a_lap_slow<T, D, ORDER>(f, acc, idx, c, pc, Nc);
-    return {f.cLF * __ll2double_rn(s1x - 2 * D * cc.x), f.cLF * __ll2double_rn(s1y - 2 * D * cc.y)};
+    if (bad) {
+      const double2 aL = a_lap_slow<T, D, ORDER>(f, acc, idx, c, pc, Ng * f.cLF);
+      return {aL.x * f.invcLF, aL.y * f.invcLF};
+    }
+    return {i2d_rn(s1x - 2 * D * cc.x), i2d_rn(s1y - 2 * D * cc.y)};
   }
   long long s2x = 0, s2y = 0;
 #pragma unroll
@@ -350,10 +365,13 @@ __device__ __forceinline__ double2 a_lap_exact_deep(const Field<T>& f, const Acc
     s2x += lo.x + hi.x;
     s2y += lo.y + hi.y;
   }
-  if (bad) return a_lap_slow<T, D, ORDER>(f, acc, idx, c, pc, Nc);
+  if (bad) {
+    const double2 aL = a_lap_slow<T, D, ORDER>(f, acc, idx, c, pc, Ng * f.cLF);
+    return {aL.x * f.invcLF, aL.y * f.invcLF};
+  }
   const long long Sx = 16 * s1x - s2x - 30 * D * cc.x;
   const long long Sy = 16 * s1y - s2y - 30 * D * cc.y;
-  return {f.cLF * __ll2double_rn(Sx), f.cLF * __ll2double_rn(Sy)};
+  return {i2d_rn(Sx), i2d_rn(Sy)};
 }
 
 template <class T, int D>
@@ -376,6 +394,7 @@ struct StageArgs {
   double dt6;                  // dt/6 in FP64 (PMix stage 4)
   int stage;                   // 0 = write F only, 1..4 = RK4 stage
   unsigned int* flag;          // bit 0: non-finite Psi
+  const typename T::VR* Vs;    // exact-sum stages: V / cLF (nullptr when V is)
   int xwall;                   // 3D tiled path: the shell also owns x in [2, 1 + xwall] and its mirror
                                // (deep-interior kernels start at x = 2 + xwall); 0 by default
 };
@@ -425,12 +444,13 @@ struct PointVals {
   typename T::M mst;    // master Psi^n, stage 4
 };
 
-// S = the stage when known at compile time, -1 = read A.stage.
-template <class T, int S = -1>
+// S = the stage when known at compile time, -1 = read A.stage.  G: the
+// exact-sum stages, which read the scaled potential V / cLF (see rk_apply).
+template <class T, int S = -1, bool G = false>
 __device__ __forceinline__ PointVals<T> load_point(const StageArgs<T>& A, int64_t i, bool with_v) {
   PointVals<T> p;
   const int st = (S >= 0) ? S : A.stage;
-  p.v = with_v ? ldv<typename T::R>(A.f.V, i) : typename T::R(0);
+  p.v = with_v ? ldv<typename T::R>(G ? A.Vs : A.f.V, i) : typename T::R(0);
   if (st >= 1 && st <= 3) p.pn = A.psin[i];
   if (st >= 2) p.K = A.ktot[i];
   if (st == 4) p.mst = A.master[i];
@@ -444,8 +464,8 @@ __device__ __forceinline__ void rk_apply(const StageArgs<T>& A, int64_t i, typen
   using R = typename T::R;
   using C = typename T::C;
   switch ((S >= 0) ? S : A.stage) {
-    case 0:
-      A.out[i] = C{F.x, F.y};
+    case 0:  // F itself: dtc = 1, or cLF for the exact-sum stages (whose F is in units of cLF)
+      A.out[i] = C{A.dtc * F.x, A.dtc * F.y};
       break;
     case 1:  // K_tot = k; Psi_tmp = Psi^n + (dt/2) k
       A.ktot[i] = C{F.x, F.y};
@@ -529,7 +549,8 @@ __device__ __forceinline__ void process_site_pv(const StageArgs<T>& A, const Acc
   using C2 = typename V2<R>::t;
   const Field<T>& f = A.f;
   const C2 pc = acc.at0();
-  const R Nc = fma(f.s, norm2(pc), -p.v);
+  // exact-sum stages work in units of cLF: Nc / cLF (p.v holds V / cLF there)
+  const R Nc = fma(EXACT ? f.sG : f.s, norm2(pc), -p.v);
   C2 aL;
   if constexpr (EXACT) aL = a_lap_exact<T, D, ORDER>(f, acc, idx, c, pc, Nc);
   else aL = a_lap<T, D, ORDER>(f, acc, idx, c, pc, Nc);
@@ -544,7 +565,7 @@ __device__ __forceinline__ void process_site_pv(const StageArgs<T>& A, const Acc
 
 template <class T, int D, int ORDER, bool EXACT, class Acc>
 __device__ __forceinline__ void process_site(const StageArgs<T>& A, const Acc& acc, const int* idx, int64_t c) {
-  process_site_pv<T, D, ORDER, EXACT>(A, acc, idx, c, load_point<T>(A, c, true));
+  process_site_pv<T, D, ORDER, EXACT>(A, acc, idx, c, load_point<T, -1, EXACT>(A, c, true));
 }
 
 // How a stage is launched: kernel variant, CTA tile, and (3D tiled kernel)

@@ -26,5 +26,6 @@ cudaError_t launch_energy(const Field<T>& f, double scale, double* partials, dou
                           cudaStream_t stream);
 cudaError_t launch_vmax(const void* V, bool v_double, int64_t total, unsigned long long* out, cudaStream_t stream);
 cudaError_t launch_round_master(const double2* master, float2* n32, int64_t total, cudaStream_t stream);
+cudaError_t launch_scale_v(const double* V, double s, int64_t n, double* Vs, cudaStream_t stream);
 
 }  // namespace nlse

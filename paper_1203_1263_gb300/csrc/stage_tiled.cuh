@@ -142,9 +142,9 @@ __global__ void __launch_bounds__(TX* TY) k_stage3d_tiled(const StageArgs<T> A, 
         for (int d = 0; d < 5; ++d) acc.p[d] = ring + ring6(z - 2 + d) * PS;
         acc.w = W;
         acc.o = o;
-        const PointVals<T> pv = load_point<T>(A, c, f.V != nullptr);
+        const PointVals<T> pv = load_point<T, -1, true>(A, c, f.V != nullptr);
         const auto pc = acc.at0();
-        const auto Nc = fma(f.s, norm2(pc), -pv.v);
+        const auto Nc = fma(f.sG, norm2(pc), -pv.v);   // units of cLF
         const auto aL = a_lap_exact_deep<T, 3, ORDER>(f, acc, idx, c, pc, Nc);
         rk_apply<T>(A, c, {-fma(Nc, pc.y, aL.y), fma(Nc, pc.x, aL.x)}, pv);
       } else {
@@ -180,7 +180,7 @@ __global__ void __launch_bounds__(TX* TY) k_stage2d_tiled(const StageArgs<T> A) 
   const bool deep = gx >= 2 && gx <= nx - 3 && gy >= 2 && gy <= ny - 3;   // wall shell: shell kernel
   const int64_t c = (int64_t)gy * nx + gx;
   PointVals<T> pv;   // requested before the tile, so that both latencies overlap
-  if (deep) pv = load_point<T>(A, c, f.V != nullptr);
+  if (deep) pv = load_point<T, -1, EXACT>(A, c, f.V != nullptr);
 #pragma unroll
   for (int i = 0; i < NPER; ++i) {
     const int e = tid + i * NT;
@@ -200,7 +200,7 @@ __global__ void __launch_bounds__(TX* TY) k_stage2d_tiled(const StageArgs<T> A) 
       acc.w = W;
       acc.o = (threadIdx.y + 2) * W + threadIdx.x + 2;
       const auto pc = acc.at0();
-      const auto Nc = fma(f.s, norm2(pc), -pv.v);
+      const auto Nc = fma(f.sG, norm2(pc), -pv.v);   // units of cLF
       const auto aL = a_lap_exact_deep<T, 2, ORDER>(f, acc, idx, c, pc, Nc);
       rk_apply<T>(A, c, {-fma(Nc, pc.y, aL.y), fma(Nc, pc.x, aL.x)}, pv);
     } else {

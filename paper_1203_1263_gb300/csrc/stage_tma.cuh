@@ -150,14 +150,14 @@ __global__ void __launch_bounds__(TX* TYT) k_stage3d_tma(const StageArgs<T> A, c
   PointVals<T> pv_next[RY];
 #pragma unroll
   for (int r = 0; r < RY; ++r)
-    if (deep[r]) pv_next[r] = load_point<T, S>(A, zb * plane + col[r], with_v);
+    if (deep[r]) pv_next[r] = load_point<T, S, EXACT>(A, zb * plane + col[r], with_v);
   bool aborted = false;
   for (int z = zb; z < ze; ++z) {
     PointVals<T> pv[RY];
 #pragma unroll
     for (int r = 0; r < RY; ++r) {
       pv[r] = pv_next[r];
-      if (deep[r] && z + 1 < ze) pv_next[r] = load_point<T, S>(A, (z + 1) * plane + col[r], with_v);
+      if (deep[r] && z + 1 < ze) pv_next[r] = load_point<T, S, EXACT>(A, (z + 1) * plane + col[r], with_v);
     }
     late |= !mbar_wait_bounded(smem_u32(bars + wslot), wpar, spin_limit);
     pl[4] = reinterpret_cast<const C*>(slots + wslot * G::kSlot);
@@ -175,7 +175,7 @@ __global__ void __launch_bounds__(TX* TYT) k_stage3d_tma(const StageArgs<T> A, c
         acc.w = G::W;
         acc.o = o[r];
         const auto pc = acc.at0();
-        const R Nc = fma(f.s, norm2(pc), -pv[r].v);
+        const R Nc = fma(f.sG, norm2(pc), -pv[r].v);   // units of cLF (pv holds V / cLF)
         const auto aL = a_lap_exact_deep<T, 3, ORDER>(f, acc, idx, c, pc, Nc);
         rk_apply<T, S>(A, c, {-fma(Nc, pc.y, aL.y), fma(Nc, pc.x, aL.x)}, pv[r]);
       } else {
@@ -304,7 +304,7 @@ __global__ void __launch_bounds__(TX* TYT, 3) k_stage3d_tma_exact(const StageArg
 #pragma unroll
   for (int r = 0; r < RY; ++r)
     if (deep[r]) {
-      pv_next[r] = load_point<T, S>(A, zb * plane + col[r], with_v);
+      pv_next[r] = load_point<T, S, true>(A, zb * plane + col[r], with_v);
       pc_next[r] = f.in[zb * plane + col[r]];
     }
   bool aborted = false;
@@ -316,7 +316,7 @@ __global__ void __launch_bounds__(TX* TYT, 3) k_stage3d_tma_exact(const StageArg
       pv[r] = pv_next[r];
       pcs[r] = pc_next[r];
       if (deep[r] && z + 1 < ze) {
-        pv_next[r] = load_point<T, S>(A, (z + 1) * plane + col[r], with_v);
+        pv_next[r] = load_point<T, S, true>(A, (z + 1) * plane + col[r], with_v);
         pc_next[r] = f.in[(z + 1) * plane + col[r]];
       }
     }
@@ -354,14 +354,17 @@ __global__ void __launch_bounds__(TX* TYT, 3) k_stage3d_tma_exact(const StageArg
         Sy = 16 * s1y - s2y - 90 * cc.y;
       }
       const double2 pc = pcs[r];
-      const double Nc = fma(f.s, norm2(pc), -pv[r].v);
+      // the exact-sum stages work in units of cLF: the integer sum needs no scaling, N_c is
+      // formed from s / cLF and V / cLF, and the stage coefficients carry the cLF
+      const double Nc = fma(f.sG, norm2(pc), -pv[r].v);
       double2 aL;
       if (!bad) {
-        aL = {f.cLF * i2d_rn(Sx), f.cLF * i2d_rn(Sy)};
+        aL = {i2d_rn(Sx), i2d_rn(Sy)};
       } else {   // an operand out of the fixed-point range: the FP64 stencil from global memory
         const int idx[3] = {z, gy[r], gx};
         const GAcc<T, 3> ga(f, c);
-        aL = a_lap_slow<T, 3, ORDER>(f, ga, idx, c, pc, Nc);
+        aL = a_lap_slow<T, 3, ORDER>(f, ga, idx, c, pc, Nc * f.cLF);
+        aL = {aL.x * f.invcLF, aL.y * f.invcLF};
       }
       rk_apply<T, S>(A, c, {-fma(Nc, pc.y, aL.y), fma(Nc, pc.x, aL.x)}, pv[r]);
     }
