@@ -63,7 +63,7 @@ CHUNK = 56   # steps per frame in the end-to-end measurement (the 87x87x203 run'
 # from one ncu capture (profiles/), or None when the kernels changed since.
 LAUNCHES_PER_STEP = 16   # 3D, every extent >= 7 (x >= 10): per stage 1 deep-interior + 3 wall-slab kernels
 TRAFFIC_PER_STEP = {  # one ncu capture of trap_vortex_3d_256x256x512, current kernels
-    "c128": 10708.4e6,
+    "c128": 10819.8e6,
     "c64": 5461.3e6,
     "c64_acc64": 6230.8e6,
 }
