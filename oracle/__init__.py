@@ -7,7 +7,9 @@ library.  Every function takes complex128 numpy arrays in C order and
 returns new arrays; nothing is modified in place.
 
 Parity status of each function (pins are in tests/test_oracle_pins.py):
-  evalF, laplacian, rk4      pinned (closed forms, exact solitons, brute force)
+  evalF, laplacian, rk4      pinned (closed forms, exact solitons, brute force;
+                             the L0 boundary by its pointwise boundary ODE and
+                             multilinear fields in a constant potential)
   mass                       pinned (closed form, exact-sum comparison)
   energy                     pinned (conservation, closed form for sine modes)
   stability_bound            pinned (numbers printed in Sec. 4 and Sec. 3.4)
@@ -30,6 +32,7 @@ _lib = None
 
 BC_DIRICHLET = 0
 BC_MSD = 1
+BC_L0 = 2
 
 
 def build(force: bool = False) -> str:

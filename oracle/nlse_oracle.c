@@ -29,6 +29,8 @@
  *                (Eq. BCMSDlap with Im(i z) = Re(z) and the CD value D_{b-1}),
  *                N = s|Psi|^2 - V.  When |Psi_{b-1}|^2 <= 1e-300 the ratio
  *                term is taken as 0.
+ *     L0:        dPsi_b/dt = i (s|Psi_b|^2 - V_b) Psi_b (Eq. BCL0dt);
+ *                D_b = 0 (Eq. BCL0lap).
  *     The boundary D_b enters only the 2SHOC step 2 of interior sites.
  *
  *   RK4: the ten-step algorithmic form of Sec. 3.1, Eq. RK4, with
@@ -53,6 +55,7 @@
 
 #define BC_DIRICHLET 0
 #define BC_MSD 1
+#define BC_L0 2
 #define MSD_TINY 1e-300
 
 typedef struct {
@@ -77,7 +80,7 @@ static int setup(grid *g, int d, const int64_t *n, double h, double a, double s,
     g->total *= n[k];
   }
   g->h = h; g->a = a; g->s = s; g->V = V; g->bc = bc; g->order = order;
-  if (!(order == 2 || order == 4) || !(bc == BC_DIRICHLET || bc == BC_MSD)) return -1;
+  if (!(order == 2 || order == 4) || !(bc == BC_DIRICHLET || bc == BC_MSD || bc == BC_L0)) return -1;
   return 0;
 }
 
@@ -129,7 +132,8 @@ static void compute_D_interior(const grid *g, const double *psi, double *D) {
 }
 
 /* boundary sites: the Laplacian forms of the boundary conditions,
- * Eqs. BCDlap (Dirichlet) and BCMSDlap (MSD).  Needs the interior D first. */
+ * Eqs. BCDlap (Dirichlet), BCMSDlap (MSD) and BCL0lap (L0).  Needs the
+ * interior D first. */
 static void compute_D_boundary(const grid *g, const double *psi, double *D) {
 #pragma omp parallel for schedule(static)
   for (int64_t p = 0; p < g->total; ++p) {
@@ -139,6 +143,9 @@ static void compute_D_boundary(const grid *g, const double *psi, double *D) {
       const double f = -(1.0 / g->a) * Nat(g, psi, p);
       D[2 * p] = f * re;
       D[2 * p + 1] = f * im;
+    } else if (g->bc == BC_L0) {
+      D[2 * p] = 0.0;
+      D[2 * p + 1] = 0.0;
     } else {
       const int64_t q = inward(g, p);
       const double qr = psi[2 * q], qi = psi[2 * q + 1];
@@ -214,13 +221,18 @@ static void evalF(const grid *g, const double *psi, double *F, double *D, double
     F[2 * p] = -g->a * L[2 * p + 1] - g->s * m2 * im + v * im;
     F[2 * p + 1] = g->a * L[2 * p] + g->s * m2 * re - v * re;
   }
-  /* Step 4: boundary sites, Eqs. BCDdt / msd */
+  /* Step 4: boundary sites, Eqs. BCDdt / msd / BCL0dt */
 #pragma omp parallel for schedule(static)
   for (int64_t p = 0; p < g->total; ++p) {
     if (!is_boundary(g, p)) continue;
     if (g->bc == BC_DIRICHLET) {
       F[2 * p] = 0.0;
       F[2 * p + 1] = 0.0;
+    } else if (g->bc == BC_L0) {
+      /* i N_b Psi_b */
+      const double nb = Nat(g, psi, p);
+      F[2 * p] = -nb * psi[2 * p + 1];
+      F[2 * p + 1] = nb * psi[2 * p];
     } else {
       const int64_t q = inward(g, p);
       const double qr = psi[2 * q], qi = psi[2 * q + 1];

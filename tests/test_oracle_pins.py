@@ -224,6 +224,105 @@ def test_plane_wave_msd(shape, k, order):
 
 
 # ---------------------------------------------------------------------------
+# Laplacian-zero boundary (Sec. 3.3, Eqs. BCL0dt and BCL0lap)
+# ---------------------------------------------------------------------------
+
+def _boundary_mask(shape):
+    m = np.zeros(shape, dtype=bool)
+    for ax in range(len(shape)):
+        idx = [slice(None)] * len(shape)
+        idx[ax] = 0
+        m[tuple(idx)] = True
+        idx[ax] = -1
+        m[tuple(idx)] = True
+    return m
+
+
+def scalar_rk4_array(z, dt, nsteps, rate):
+    """scalar_rk4 applied elementwise to an array of initial values."""
+    f = lambda y: 1j * rate(np.abs(y) ** 2) * y
+    for _ in range(nsteps):
+        k1 = f(z); k2 = f(z + dt / 2 * k1); k3 = f(z + dt / 2 * k2); k4 = f(z + dt * k3)
+        z = z + dt / 6 * (k1 + 2 * k2 + 2 * k3 + k4)
+    return z
+
+
+@pytest.mark.parametrize("shape", [(10,), (7, 9), (6, 7, 8)])
+@pytest.mark.parametrize("order", [2, 4])
+def test_l0_boundary_sites_follow_their_own_ode(shape, order):
+    """Under L0 the time derivative at a boundary site involves that site alone
+    (Eq. BCL0dt), so whatever the interior does, every boundary site is the
+    scalar RK4 iterate of z' = i(s|z|^2 - V_b) z from its own initial value."""
+    h, a, s, dt, n = 0.3, 0.7, 1.2, 0.002, 20
+    psi = W.random_field(shape, seed=51)
+    V = W.random_potential(shape, seed=52, scale=2.0)
+    out = O.rk4(psi, h, a, s, dt, n, V, W.BC_L0, order)
+    b = _boundary_mask(shape)
+    Vb = V[b]
+    expect = scalar_rk4_array(psi[b], dt, n, lambda m2: s * m2 - Vb)
+    assert np.max(np.abs(out[b] - expect)) < 1e-13
+    assert np.max(np.abs(out[~b] - psi[~b])) > 1e-3          # the interior moved
+
+
+def _multilinear_field(shape, h, seed):
+    """A complex combination of the monomials prod_{k in S} x_k (S any subset of
+    the axes).  Each is harmonic, and every central second difference of it
+    vanishes exactly, so the CD and 2SHOC Laplacians of it are 0 at every
+    interior site, provided the boundary Laplacian is 0."""
+    axes = [np.arange(N) * h - 0.5 * (N - 1) * h for N in shape]
+    grids = np.meshgrid(*axes, indexing="ij")
+    d = len(shape)
+    c = W.random_field((2 ** d,), seed=seed)
+    psi = np.zeros(shape, dtype=np.complex128)
+    for m in range(2 ** d):
+        term = np.ones(shape)
+        for k in range(d):
+            if m >> k & 1:
+                term = term * grids[k]
+        psi += c[m] * term
+    return psi
+
+
+@pytest.mark.parametrize("shape", [(11,), (8, 9), (6, 7, 8)])
+@pytest.mark.parametrize("order", [2, 4])
+def test_l0_harmonic_field_in_constant_potential(shape, order):
+    """s = 0, V = V0: with D_b = 0 (Eq. BCL0lap) every Laplacian of a multilinear
+    field is 0, so each site, boundary ones included (Eq. BCL0dt), is multiplied
+    by R(-i V0 dt) per step.  Dirichlet's D_b = V0 Psi_b / a (and its F_b = 0)
+    would not give this."""
+    h, a, V0, dt, n = 0.25, 0.9, 0.7, 0.01, 25
+    psi = _multilinear_field(shape, h, seed=53)
+    V = np.full(shape, V0)
+    out = O.rk4(psi, h, a, 0.0, dt, n, V, W.BC_L0, order)
+    expect = psi * rk4_amplification(-1j * V0 * dt) ** n
+    assert np.max(np.abs(out - expect)) < 1e-13 * np.max(np.abs(psi))
+    assert np.max(np.abs(O.rk4(psi, h, a, 0.0, dt, n, V, W.BC_DIRICHLET, order) - expect)) > 1e-4
+    # the energy density reduces to V0 |Psi|^2 on the interior
+    inner = tuple(slice(1, -1) for _ in shape)
+    e = h ** len(shape) * math.fsum((V0 * np.abs(psi[inner]) ** 2).ravel().tolist())
+    assert abs(O.energy(psi, h, a, 0.0, V, W.BC_L0, order) - e) < 1e-12 * abs(e)
+
+
+@pytest.mark.parametrize("shape", [(9,), (7, 8), (5, 6, 7)])
+@pytest.mark.parametrize("order", [2, 4])
+def test_uniform_background_l0(shape, order):
+    rho, phi, s, a, dt, n = 0.9, -0.7, 1.0, 0.8, 0.01, 30
+    z0 = math.sqrt(rho) * complex(math.cos(phi), math.sin(phi))
+    out = O.rk4(np.full(shape, z0, dtype=np.complex128), 0.2, a, s, dt, n, None, W.BC_L0, order)
+    assert np.max(np.abs(out - scalar_rk4(z0, dt, n, lambda m2: s * m2))) < 1e-13
+
+
+@pytest.mark.parametrize("shape", [(12,), (8, 9), (5, 6, 7)])
+@pytest.mark.parametrize("order", [2, 4])
+def test_l0_is_dirichlet_for_the_free_linear_equation(shape, order):
+    """With s = 0 and V = 0 both boundary forms reduce to F_b = 0 and D_b = 0."""
+    psi = W.random_field(shape, seed=54)
+    a1 = O.rk4(psi, 0.3, 0.8, 0.0, 0.003, 9, None, W.BC_L0, order)
+    a2 = O.rk4(psi, 0.3, 0.8, 0.0, 0.003, 9, None, W.BC_DIRICHLET, order)
+    assert np.array_equal(a1, a2)
+
+
+# ---------------------------------------------------------------------------
 # P6: brute force over the printed stencil tables; polynomial exactness
 # ---------------------------------------------------------------------------
 
@@ -348,7 +447,7 @@ def test_energy_closed_form(shape, modes, order):
     assert abs(got - expect) < 1e-12 * abs(expect)
 
 
-@pytest.mark.parametrize("bc", [W.BC_DIRICHLET, W.BC_MSD])
+@pytest.mark.parametrize("bc", [W.BC_DIRICHLET, W.BC_MSD, W.BC_L0])
 def test_energy_counts_interior_sites_only(bc):
     """Every term of the energy density carries a factor of the site's own Psi,
     so a field that vanishes on the interior has zero energy whatever its walls hold."""
@@ -406,7 +505,7 @@ def test_vortex_rotation_symmetry():
     assert np.max(np.abs(out - p.psi0)) > 1e-3      # it did evolve
 
 
-@pytest.mark.parametrize("bc", [W.BC_DIRICHLET, W.BC_MSD])
+@pytest.mark.parametrize("bc", [W.BC_DIRICHLET, W.BC_MSD, W.BC_L0])
 def test_split_continuation_bitwise(bc):
     psi = W.random_field((9, 10), seed=31)
     V = W.random_potential((9, 10), seed=32)
