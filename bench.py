@@ -203,9 +203,9 @@ def run_ours(args, rank, world, local_rank):
     sites = p.sites
     stream = torch.cuda.Stream(dev)
 
-    def timed(dtype, K, Wm):
+    def timed(dtype, K, Wm, bc="msd"):
         with torch.cuda.stream(stream):
-            g = Integrator(p.psi0, p.h, p.a, p.s, p.V, "msd", p.order, dtype, device=dev, stream=stream)
+            g = Integrator(p.psi0, p.h, p.a, p.s, p.V, bc, p.order, dtype, device=dev, stream=stream)
             if args.variant is not None or args.tile != -1:
                 g.set_kernel(args.variant if args.variant is not None else (2 if dtype == "c128" else 1), args.tile)
             g.step(Wm, dt)
@@ -270,6 +270,14 @@ def run_ours(args, rank, world, local_rank):
             forms[dt_name] = {"value": round(v2, 4), "unit": UNIT, "speedup_vs_f64": round(v2 / value, 3),
                               "rel_l2_vs_f64_gpu": rl2, "roofline": r2}
             g2.close()
+        # the Laplacian-zero boundary (Eqs. BCL0dt, BCL0lap) on the same grid: only the wall kernels differ
+        for dt_name in ("c128", "c64"):
+            g3, ms3, _, _ = timed(dt_name, K, Wm, "l0")
+            v3 = sites * K / (ms3 * 1e-3) / 1e9
+            r3, _ = roofline_for(dt_name, sites, ms3 * 1e-3 / K, p.V is not None)
+            r3["traffic"] = None
+            forms[dt_name + "_l0"] = {"value": round(v3, 4), "unit": UNIT, "bc": "l0", "roofline": r3}
+            g3.close()
         result["forms"] = forms
 
     if not args.no_batch and rank == 0:

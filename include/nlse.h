@@ -52,6 +52,8 @@ extern "C" {
 /* ---- boundary conditions (Sec. 3.3) ---- */
 #define NLSE_BC_DIRICHLET 0 /* Eq. BCDdef: Psi_b is held at its value; Laplacian form Eq. BCDlap */
 #define NLSE_BC_MSD       1 /* Eq. BCMSDdef: |Psi_b|^2 held; Eq. msd and Eq. BCMSDlap */
+#define NLSE_BC_L0        2 /* Laplacian-zero: dPsi_b/dt = i(s|Psi_b|^2 - V_b) Psi_b (Eq. BCL0dt),
+                               Laplacian form D_b = 0 (Eq. BCL0lap) */
 
 /* ---- precision forms ---- */
 #define NLSE_C128      0 /* FP64 throughout */

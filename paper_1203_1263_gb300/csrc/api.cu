@@ -384,7 +384,8 @@ int nlse_create(nlse_t* out, int dims, const int64_t* N, double h, double a, dou
   if (!(h > 0) || !isfinite(h)) return fail(NLSE_EINVAL, "h must be > 0");
   if (!(a > 0) || !isfinite(a)) return fail(NLSE_EINVAL, "a must be > 0");
   if (!isfinite(s)) return fail(NLSE_EINVAL, "s must be finite");
-  if (bc != NLSE_BC_DIRICHLET && bc != NLSE_BC_MSD) return fail(NLSE_EINVAL, "bc must be 0 or 1");
+  if (bc != NLSE_BC_DIRICHLET && bc != NLSE_BC_MSD && bc != NLSE_BC_L0)
+    return fail(NLSE_EINVAL, "bc must be 0, 1 or 2");
   if (order != 2 && order != 4) return fail(NLSE_EINVAL, "order must be 2 or 4");
   if (!psi) return fail(NLSE_EINVAL, "psi is NULL");
   if (!workspace) return fail(NLSE_EINVAL, "workspace is NULL");

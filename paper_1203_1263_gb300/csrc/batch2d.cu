@@ -310,7 +310,8 @@ int validate(int nruns, const nlse_run_desc* runs) {
       return bfail(NLSE_EINVAL, "every run needs 3 <= N <= 2^20 on both axes");
     if (!(d.h > 0) || !(d.a > 0) || !isfinite(d.s) || !(d.dt > 0)) return bfail(NLSE_EINVAL, "run h, a, dt must be > 0");
     if (d.order != 2 && d.order != 4) return bfail(NLSE_EINVAL, "run order must be 2 or 4");
-    if (d.bc != NLSE_BC_DIRICHLET && d.bc != NLSE_BC_MSD) return bfail(NLSE_EINVAL, "run bc must be 0 or 1");
+    if (d.bc != NLSE_BC_DIRICHLET && d.bc != NLSE_BC_MSD && d.bc != NLSE_BC_L0)
+      return bfail(NLSE_EINVAL, "run bc must be 0, 1 or 2");
     if (!d.psi || (uintptr_t)d.psi % 8) return bfail(NLSE_EINVAL, "run psi must be an 8-byte aligned device pointer");
     const double rho = (d.order == 4 ? 32.0 / 3.0 : 8.0) / (d.h * d.h);
     if (d.dt > 2.0 * sqrt(2.0) / (d.a * rho)) return bfail(NLSE_EUNSTABLE, "a run's dt exceeds its RK4 linear bound");

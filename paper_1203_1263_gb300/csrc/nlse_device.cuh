@@ -5,9 +5,10 @@
 // and then the fused RK4 update of Eq. RK4_GPU for that stage.  Boundary
 // sites are updated by the interior site that is their "b-1" neighbour (one
 // step inward along every axis on which the boundary site sits on a face),
-// with F_b = 0 (Dirichlet, Eq. BCDdt) or F_b = i Im(F_c / Psi_c) Psi_b (MSD,
-// Eq. msd).  Every boundary site has exactly one such interior site, so each
-// site of the grid is written by exactly one thread per stage.
+// with F_b = 0 (Dirichlet, Eq. BCDdt), F_b = i Im(F_c / Psi_c) Psi_b (MSD,
+// Eq. msd) or F_b = i (s|Psi_b|^2 - V_b) Psi_b (L0, Eq. BCL0dt).  Every
+// boundary site has exactly one such interior site, so each site of the grid
+// is written by exactly one thread per stage.
 //
 // Laplacian.  Order 2 is the central difference (step 1 of Eqs. 2shoc1d,
 // 2d2shocs1, 3d2shocs).  Order 4 is 2SHOC (Eqs. 2shoc1d2, 2d2shocs2,
@@ -17,8 +18,8 @@
 // (expand D = Lap_CD Psi in the step-2 stencil: the cross terms of the
 // neighbour D's cancel against the edge-diagonal Psi terms), which needs no
 // D array and a third of the arithmetic.  Where a face neighbour b of c is a
-// boundary site, 2SHOC uses the boundary Laplacian form D_b (Eq. BCDlap or
-// Eq. BCMSDlap) instead of the central difference at b; the same five-point
+// boundary site, 2SHOC uses the boundary Laplacian form D_b (Eq. BCDlap,
+// Eq. BCMSDlap, or D_b = 0 by Eq. BCL0lap) instead of the central difference at b; the same five-point
 // form still holds if the missing value Psi_{+-2} beyond the wall is replaced
 // by the "ghost" g that makes the central difference at b equal D_b:
 //     g = h^2 D_b - Psi_c - sum_{in-face neighbours of b} Psi + 2d Psi_b.
@@ -31,7 +32,7 @@
 
 namespace nlse {
 
-enum { BC_DIRICHLET = 0, BC_MSD = 1 };
+enum { BC_DIRICHLET = 0, BC_MSD = 1, BC_L0 = 2 };
 
 template <class R> struct V2;
 template <> struct V2<double> { using t = double2; };
@@ -109,8 +110,8 @@ struct GAcc {
   __device__ __forceinline__ longlong2 fx1(int k, int s) const;
 };
 
-// h^2 D_b at the face boundary site nb = c + dir e_k (Eqs. BCDlap, BCMSDlap),
-// then the ghost value beyond the wall.
+// h^2 D_b at the face boundary site nb = c + dir e_k (Eqs. BCDlap, BCMSDlap;
+// 0 under L0, Eq. BCL0lap), then the ghost value beyond the wall.
 template <class T, int D, class Acc>
 __device__ __forceinline__ typename V2<typename T::R>::t ghost(const Field<T>& f, const Acc& acc, int k, int dir,
                                                                int64_t c, typename V2<typename T::R>::t pc,
@@ -119,14 +120,16 @@ __device__ __forceinline__ typename V2<typename T::R>::t ghost(const Field<T>& f
   using R = typename T::R;
   using C2 = typename V2<R>::t;
   const C2 pb = acc.at1(k, dir);
-  const R Nb = fma(f.s, norm2(pb), -ldv<R>(f.V, c + dir * f.st[k]));
-  R fac;
-  if (f.bc == BC_DIRICHLET) {
-    fac = -f.h2_over_a * Nb;
-  } else {
-    const R m2 = norm2(pc);
-    const R ratio = (m2 > f.tiny) ? fma(dh_c.x, pc.x, dh_c.y * pc.y) / m2 : R(0);
-    fac = fma(f.h2_over_a, Nc - Nb, ratio);
+  R fac = R(0);
+  if (f.bc != BC_L0) {
+    const R Nb = fma(f.s, norm2(pb), -ldv<R>(f.V, c + dir * f.st[k]));
+    if (f.bc == BC_DIRICHLET) {
+      fac = -f.h2_over_a * Nb;
+    } else {
+      const R m2 = norm2(pc);
+      const R ratio = (m2 > f.tiny) ? fma(dh_c.x, pc.x, dh_c.y * pc.y) / m2 : R(0);
+      fac = fma(f.h2_over_a, Nc - Nb, ratio);
+    }
   }
   C2 g = {fma(R(2 * D), pb.x, fma(fac, pb.x, -pc.x)), fma(R(2 * D), pb.y, fma(fac, pb.y, -pc.y))};
 #pragma unroll
@@ -501,9 +504,10 @@ __device__ __forceinline__ void rk_update(const StageArgs<T>& A, int64_t i, type
 
 // Update every boundary site whose b-1 neighbour is the interior site c
 // (c + sum_k o_k e_k with o_k in {0} u {-1 if idx==1} u {+1 if idx==n-2}, not
-// all 0), with F_b = 0 (Dirichlet) or F_b = i Im(F_c / Psi_c) Psi_b (MSD).
+// all 0), with F_b = 0 (Dirichlet), F_b = i Im(F_c / Psi_c) Psi_b (MSD) or
+// F_b = i N_b Psi_b (L0; in units of cLF on the exact-sum stages, like F_c).
 // Out of line: only sites next to a wall call it.
-template <class T, int D, class Acc>
+template <class T, int D, bool EXACT, class Acc>
 __device__ __forceinline__ void serve_walls(const StageArgs<T>& A, const Acc& acc, const int* idx, int64_t c,
                                          typename V2<typename T::R>::t pc, typename V2<typename T::R>::t F) {
   using R = typename T::R;
@@ -534,6 +538,10 @@ __device__ __forceinline__ void serve_walls(const StageArgs<T>& A, const Acc& ac
     if (f.bc == BC_MSD) {
       const C2 pb = acc.atv(o);
       Fb = {-theta * pb.y, theta * pb.x};
+    } else if (f.bc == BC_L0) {
+      const C2 pb = acc.atv(o);
+      const R Nb = fma(EXACT ? f.sG : f.s, norm2(pb), -ldv<R>(EXACT ? A.Vs : f.V, b));
+      Fb = {-Nb * pb.y, Nb * pb.x};
     }
     rk_update<T>(A, b, Fb);
   }
@@ -560,7 +568,7 @@ __device__ __forceinline__ void process_site_pv(const StageArgs<T>& A, const Acc
   bool near = false;
 #pragma unroll
   for (int k = 0; k < D; ++k) near |= (idx[k] == 1) | (idx[k] == f.n[k] - 2);
-  if (near) serve_walls<T, D>(A, acc, idx, c, pc, F);
+  if (near) serve_walls<T, D, EXACT>(A, acc, idx, c, pc, F);
 }
 
 template <class T, int D, int ORDER, bool EXACT, class Acc>

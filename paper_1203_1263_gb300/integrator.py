@@ -15,7 +15,7 @@ import torch
 from . import _lib as L
 
 _DTYPES = {"c128": L.C128, "c64": L.C64, "c64_acc64": L.C64_ACC64}
-_BCS = {"dirichlet": L.BC_DIRICHLET, "msd": L.BC_MSD}
+_BCS = {"dirichlet": L.BC_DIRICHLET, "msd": L.BC_MSD, "l0": L.BC_L0}
 
 
 def _code(table, v):
@@ -39,7 +39,7 @@ class Integrator:
     """RK4 integrator of i Psi_t + a Lap Psi - V Psi + s|Psi|^2 Psi = 0 on one GPU.
 
     psi0   complex array (numpy or torch), shape (N0[, N1[, N2]]), C order
-    h, a, s, V (real array or None), bc ('dirichlet' | 'msd'), order (2 | 4)
+    h, a, s, V (real array or None), bc ('dirichlet' | 'msd' | 'l0'), order (2 | 4)
     dtype  'c128' (FP64), 'c64' (FP32), 'c64_acc64' (FP32 stages, FP64 master and accumulator)
     """
 
@@ -144,7 +144,7 @@ class BatchIntegrator:
     """Many independent 2D runs (complex64) advanced together (nlse_batch_*).
 
     runs: sequence of dicts with psi0 (complex array (Ny, Nx)), h, a, s, dt,
-    V (real array or None), bc ('dirichlet' | 'msd'), order (2 | 4)."""
+    V (real array or None), bc ('dirichlet' | 'msd' | 'l0'), order (2 | 4)."""
 
     def __init__(self, runs, device=None, stream=None):
         self.lib = L.lib()

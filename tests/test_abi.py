@@ -50,7 +50,7 @@ def test_workspace_bytes():
 
 @pytest.mark.parametrize("args,code", [
     (dict(dims=0), L.NLSE_EINVAL), (dict(N=[2, 5, 5]), L.NLSE_EINVAL), (dict(h=0.0), L.NLSE_EINVAL),
-    (dict(a=-1.0), L.NLSE_EINVAL), (dict(order=3), L.NLSE_EINVAL), (dict(bc=5), L.NLSE_EINVAL),
+    (dict(a=-1.0), L.NLSE_EINVAL), (dict(order=3), L.NLSE_EINVAL), (dict(bc=5), L.NLSE_EINVAL), (dict(bc=3), L.NLSE_EINVAL),
     (dict(dtype=9), L.NLSE_EINVAL), (dict(psi=None), L.NLSE_EINVAL), (dict(ws=None), L.NLSE_EINVAL),
     (dict(ws_bytes=16), L.NLSE_ENOMEM), (dict(ws=4096 + 8), L.NLSE_EINVAL),
 ])

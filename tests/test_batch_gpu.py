@@ -13,6 +13,7 @@ from paper_1203_1263_gb300 import workloads as W
 from paper_1203_1263_gb300.integrator import BatchIntegrator, Integrator
 
 pytestmark = pytest.mark.gpu
+BCS = {"dirichlet": W.BC_DIRICHLET, "msd": W.BC_MSD, "l0": W.BC_L0}
 
 
 def small_runs(seed=4, nruns=14):
@@ -27,7 +28,7 @@ def small_runs(seed=4, nruns=14):
         p = W.batch_run_problem(d)
         s_rho = abs(p.s) * float(np.max(np.abs(p.psi0))) ** 2
         dt = 0.5 * O.stability_bound(2, p.h, p.a, p.order, p.vmax(), s_rho)
-        runs.append(dict(psi0=p.psi0, h=p.h, a=p.a, s=p.s, dt=dt, V=p.V, bc=["dirichlet", "msd"][i % 2],
+        runs.append(dict(psi0=p.psi0, h=p.h, a=p.a, s=p.s, dt=dt, V=p.V, bc=["dirichlet", "msd", "l0"][i % 3],
                          order=p.order))
     return runs
 
@@ -51,7 +52,7 @@ def test_batch_matches_oracle():
     b.sync()
     for i, r in enumerate(runs):
         ref = O.rk4(r["psi0"], r["h"], r["a"], r["s"], r["dt"], 12, r["V"],
-                    W.BC_DIRICHLET if r["bc"] == "dirichlet" else W.BC_MSD, r["order"])
+                    BCS[r["bc"]], r["order"])
         got = b.numpy(i).astype(np.complex128)
         err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
         assert err <= 2e-5, (i, err)

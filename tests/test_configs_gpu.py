@@ -88,6 +88,46 @@ def test_trap_vortex_256x256x512_one_step_full_size():
         g.close()
 
 
+def _boundary_mask(shape):
+    m = np.zeros(shape, dtype=bool)
+    for ax in range(len(shape)):
+        idx = [slice(None)] * len(shape)
+        idx[ax] = 0
+        m[tuple(idx)] = True
+        idx[ax] = -1
+        m[tuple(idx)] = True
+    return m
+
+
+def test_256x256x512_laplacian_zero_boundary_full_size():
+    """The benchmark's grid, potential and launch configuration with the
+    Laplacian-zero boundary (Eqs. BCL0dt, BCL0lap), on the trap state plus a
+    unit plane wave so that the walls carry a field: one step against the
+    oracle on every site; then 16 more (one graph replay), after which every
+    boundary site must be the scalar RK4 iterate of z' = i(s|z|^2 - V_b) z
+    from its own initial value, since Eq. BCL0dt involves that site alone."""
+    p = W.trap_vortex_3d(shape=(512, 256, 256))
+    x = (np.arange(p.shape[2]) - 0.5 * (p.shape[2] - 1)) * p.h
+    psi0 = p.psi0 + 0.5 * np.exp(0.4j * x)[None, None, :]
+    s_rho = abs(p.s) * float(np.max(np.abs(psi0))) ** 2
+    dt = 0.8 * O.stability_bound(3, p.h, p.a, 4, p.vmax(), s_rho)
+    ref = O.rk4(psi0, p.h, p.a, p.s, dt, 1, p.V, W.BC_L0, 4)
+    for dtype, tol in (("c128", 1e-12), ("c64", 2e-5)):
+        g = Integrator(psi0, p.h, p.a, p.s, p.V, "l0", 4, dtype)
+        g.step(1, dt)
+        assert rel_l2(g.numpy(), ref) <= tol, dtype
+        if dtype == "c128":
+            g.step(16, dt)
+            b = _boundary_mask(p.shape)
+            z, Vb = psi0[b], p.V[b]
+            f = lambda y: 1j * (p.s * np.abs(y) ** 2 - Vb) * y
+            for _ in range(17):
+                k1 = f(z); k2 = f(z + dt / 2 * k1); k3 = f(z + dt / 2 * k2); k4 = f(z + dt * k3)
+                z = z + dt / 6 * (k1 + 2 * k2 + 2 * k3 + k4)
+            assert np.max(np.abs(g.numpy()[b] - z)) <= 1e-12 * np.max(np.abs(z))
+        g.close()
+
+
 def test_trap_vortex_long_run_fp32_forms_vs_fp64():
     """3360 steps on 87x87x203 (the paper's headline step count): the FP32
     forms against the FP64 GPU run.  Within the stability bound RK4 damps

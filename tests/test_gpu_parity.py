@@ -19,7 +19,7 @@ from paper_1203_1263_gb300.integrator import Integrator
 pytestmark = pytest.mark.gpu
 
 TOL = {"c128": (1e-12, 1e-11), "c64": (2e-5, 2e-4), "c64_acc64": (2e-5, 2e-4)}
-BCS = {"dirichlet": W.BC_DIRICHLET, "msd": W.BC_MSD}
+BCS = {"dirichlet": W.BC_DIRICHLET, "msd": W.BC_MSD, "l0": W.BC_L0}
 
 SHAPES = {
     1: [(37,), (3,), (4,), (1000,)],
@@ -84,7 +84,7 @@ def oracle_rk4_cached(key, *args):
 
 @pytest.mark.parametrize("dims,shape", CASES)
 @pytest.mark.parametrize("order", [2, 4])
-@pytest.mark.parametrize("bc", ["dirichlet", "msd"])
+@pytest.mark.parametrize("bc", ["dirichlet", "msd", "l0"])
 @pytest.mark.parametrize("dtype", ["c128", "c64", "c64_acc64"])
 @pytest.mark.parametrize("variant", [0, 1, 2, 3])
 def test_step_matches_oracle(dims, shape, order, bc, dtype, variant):
@@ -102,7 +102,7 @@ def test_step_matches_oracle(dims, shape, order, bc, dtype, variant):
 
 @pytest.mark.parametrize("dims,shape", [(1, (37,)), (2, (19, 45)), (3, (9, 21, 70)), (3, (3, 4, 5))])
 @pytest.mark.parametrize("order", [2, 4])
-@pytest.mark.parametrize("bc", ["dirichlet", "msd"])
+@pytest.mark.parametrize("bc", ["dirichlet", "msd", "l0"])
 @pytest.mark.parametrize("dtype", ["c128", "c64"])
 def test_rhs_matches_oracle(dims, shape, order, bc, dtype):
     h, a, s = 0.3, 0.9, 1.3
@@ -116,7 +116,7 @@ def test_rhs_matches_oracle(dims, shape, order, bc, dtype):
 
 @pytest.mark.parametrize("dims,shape", [(1, (1000,)), (2, (70, 33)), (3, (20, 17, 64))])
 @pytest.mark.parametrize("order", [2, 4])
-@pytest.mark.parametrize("bc", ["dirichlet", "msd"])
+@pytest.mark.parametrize("bc", ["dirichlet", "msd", "l0"])
 @pytest.mark.parametrize("dtype", ["c128", "c64", "c64_acc64"])
 def test_mass_energy_match_oracle(dims, shape, order, bc, dtype):
     h, a, s = 0.25, 0.7, -0.6
@@ -155,7 +155,7 @@ def test_tiled_kernel_equals_generic_bitwise(dtype, dims, shape, tile_cfg):
     """The tiled kernels perform the generic kernel's arithmetic in the same
     order; only where the operands come from differs."""
     for order in (2, 4):
-        for bc in ("dirichlet", "msd"):
+        for bc in ("dirichlet", "msd", "l0"):
             psi, V = problem(shape, 77)
             h, a, s = 0.3, 0.6, -1.0
             dt = stable_dt(shape, h, a, s, order, V)
