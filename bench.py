@@ -286,6 +286,11 @@ def run_ours(args, rank, world, local_rank):
     if not args.no_surrogate and rank == 0:
         result.setdefault("forms", {})["surrogate"] = surrogate_form(args, dev)
 
+    if not args.no_paper_tables and rank == 0:
+        result["paper_tables"] = paper_tables(dev)
+    if args.chunk_study and rank == 0:
+        result["chunk_study"] = chunk_study(dev)
+
     # ---- end to end through the public API: pinned host Psi in, CHUNK steps, Psi and mass out ----
     if not args.no_e2e:
         import torch
@@ -323,6 +328,85 @@ def run_ours(args, rank, world, local_rank):
         dist.barrier()
         dist.destroy_process_group()
     return result
+
+
+# The paper's GPU times (seconds) for its timing workloads, 10,000 steps, chunk
+# 5000 (Sec. 7, Tables 1-3): (RK4+CD in FP32, RK4+2SHOC in FP64), GTX 580.
+PAPER_TABLE_SECONDS = {
+    1: {1000: (0.21, 0.49), 10000: (0.24, 0.67), 100000: (1.21, 4.52), 1000000: (9.41, 39.72),
+        3000000: (27.65, 117.32)},
+    2: {961: (0.29, 0.59), 10000: (0.34, 1.09), 99856: (1.76, 6.25), 1000000: (14.94, 54.65),
+        2999824: (42.15, 162.79)},
+    3: {9261: (0.59, 2.00), 97336: (2.90, 13.34), 970299: (31.85, 131.74), 2985984: (82.14, 365.47)},
+}
+
+
+def _timed_frames(p, dtype, order, dev, nsteps, chunk):
+    """Wall seconds of the paper's usage through the public API: Psi from
+    pinned host memory to the device, then nsteps in chunks of `chunk` with
+    Psi copied back to pinned host memory after each chunk."""
+    import torch
+    from paper_1203_1263_gb300.integrator import Integrator
+    host_np = p.psi0.astype(np.complex64) if dtype == "c64" else p.psi0
+    host_in = torch.from_numpy(np.ascontiguousarray(host_np)).pin_memory()
+    host_out = torch.empty_like(host_in).pin_memory()
+    stream = torch.cuda.Stream(dev)
+    with torch.cuda.stream(stream):
+        g = Integrator(p.psi0, p.h, p.a, p.s, p.V, "msd", order, dtype, device=dev, stream=stream)
+        g.step(min(chunk, 16) + 1, p.dt)      # untimed: builds the step graph
+        g.sync()
+        w0 = time.perf_counter()
+        g.psi.copy_(host_in, non_blocking=True)
+        done = 0
+        while done < nsteps:
+            n = min(chunk, nsteps - done)
+            g.step(n, p.dt)
+            host_out.copy_(g.psi, non_blocking=True)
+            stream.synchronize()
+            done += n
+        wall = time.perf_counter() - w0
+        g.sync()
+        g.close()
+    return wall
+
+
+def paper_tables(dev):
+    """The timing runs of Sec. 7 (Tables 1-3) on this GPU: the dark soliton
+    (1D), dark vortex (2D) and vortex ring (3D) workloads, 10,000 steps at
+    k = 0.005 in chunks of 5000, RK4+CD in FP32 and RK4+2SHOC in FP64."""
+    rows = []
+    for dims, table in PAPER_TABLE_SECONDS.items():
+        for total, (paper_cd, paper_2shoc) in table.items():
+            row = {"dims": dims, "sites": total}
+            for key, dtype, order, paper_s in (("cd_f32", "c64", 2, paper_cd), ("2shoc_f64", "c128", 4, paper_2shoc)):
+                p = W.paper_timing_problem(dims, total, order)
+                row["grid"] = list(p.shape)
+                try:
+                    sec = _timed_frames(p, dtype, order, dev, p.steps, 5000)
+                except RuntimeError as e:      # e.g. NLSE_ENONFINITE: the run is reported, not timed
+                    row[key] = {"error": str(e)[:200], "paper_seconds": paper_s}
+                    continue
+                row[key] = {"seconds": round(sec, 4), "Msite_step_s": round(p.sites * p.steps / sec / 1e6, 1),
+                            "paper_seconds": paper_s, "speedup_vs_paper_gpu": round(paper_s / sec, 1)}
+            rows.append(row)
+    return {"workloads": "Sec. 4 dark soliton (1D, h=0.1), dark vortex (2D, h=0.25), vortex ring (3D, h=1.5); "
+                         "MSD, k=0.005, 10,000 steps, chunks of 5000 with Psi to and from pinned host memory",
+            "paper_gpu": "GeForce GTX 580 (Sec. 7)", "rows": rows}
+
+
+def chunk_study(dev):
+    """Slowdown against chunk size (Sec. 7, chunk-size figure): 1000 steps
+    (t = 5) of the timing workloads at about 1e3 and 1e6 sites, Psi copied
+    back to the host after every chunk; slowdown = time(chunk) / time(1000)."""
+    out = []
+    for dims, sizes in ((1, (1000, 1000000)), (2, (961, 1000000)), (3, (9261, 970299))):
+        for total in sizes:
+            for key, dtype, order in (("cd_f32", "c64", 2), ("2shoc_f64", "c128", 4)):
+                p = W.paper_timing_problem(dims, total, order)
+                t = {c: _timed_frames(p, dtype, order, dev, 1000, c) for c in (1000, 100, 10, 1)}
+                out.append({"dims": dims, "sites": p.sites, "scheme": key, "seconds_chunk_1000": round(t[1000], 4),
+                            "slowdown": {str(c): round(t[c] / t[1000], 2) for c in (100, 10, 1)}})
+    return out
 
 
 def batch_form(args, dev, K, Wm):
@@ -581,6 +665,8 @@ def main():
     ap.add_argument("--sur-epochs", type=int, default=60)
     ap.add_argument("--surrogate-kernels-only", action="store_true",
                     help="print only the surrogate's kernel throughput (training and inference steps) and exit")
+    ap.add_argument("--no-paper-tables", action="store_true", help="skip the timing runs of the paper's Tables 1-3")
+    ap.add_argument("--chunk-study", action="store_true", help="also time 1000 steps in chunks of 1..1000")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--ref-budget", type=float, default=90.0)
     args = ap.parse_args()

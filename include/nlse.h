@@ -149,6 +149,8 @@ const char *nlse_last_error(void);
  *       in 64-bit fixed point on the integer pipe and converted to FP64 once,
  *   3 = generic kernel with the exact-sum stencil (NLSE_C128; else as 0).
  * Variants 0 and 1 give bit-for-bit the same result, and so do 2 and 3.
+ * Default: 2 for NLSE_C128 and 1 otherwise, except 3D grids of at most 2^18
+ * sites (NLSE_C128) or 2^21 sites (the FP32 forms), which take 3 and 0.
  * tile_cfg picks the tiled kernel's CTA tile (x-by-y threads): 0 = 32x8,
  * 1 = 64x4, 2 = 32x16, 3 = 64x8, -1 = default; it never changes results.
  * Call between nlse_step calls, not during one. */

@@ -404,7 +404,12 @@ int nlse_create(nlse_t* out, int dims, const int64_t* N, double h, double a, dou
   c->stream = (cudaStream_t)stream;
   c->ws = (char*)workspace;
   c->lay = L;
-  c->variant = (dtype == NLSE_C128) ? 2 : 1;   // FP64: exact-sum stencil
+  // FP64: exact-sum stencil.  3D grids too small to fill the GPU with the
+  // z-marching kernel's tiles x plane chunks take the one-thread-per-site
+  // kernel (measured faster up to about 2^18 sites in FP64, 2^21 in FP32).
+  c->variant = (dtype == NLSE_C128) ? 2 : 1;
+  if (dims == 3 && total <= (dtype == NLSE_C128 ? (int64_t(1) << 18) : (int64_t(1) << 21)))
+    c->variant = (dtype == NLSE_C128) ? 3 : 0;
   c->tile_cfg = -1;
   c->spin_limit = kSpinLimit;
   c->graph_dt = -1.0;

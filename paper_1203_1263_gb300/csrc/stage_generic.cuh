@@ -117,11 +117,29 @@ __global__ void __launch_bounds__(256) k_stage_shell(const StageArgs<T> A, int64
   process_site<T, D, ORDER, EXACT>(A, acc, idx, c);
 }
 
+// CTA size of the one-thread-per-site kernels: 256 threads, halved (down to
+// one warp) while the grid would give fewer than two CTAs per SM.  On small
+// grids this spreads the sites over all SMs, which matters most on the FP64
+// path (a few FP64 instructions per cycle per SM); it never changes results.
+inline int site_kernel_threads(int64_t n) {
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0, v = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0)
+      sms = v;
+    else
+      sms = 152;
+  }
+  int t = 256;
+  while (t > 32 && (n + t - 1) / t < 2 * (int64_t)sms) t >>= 1;
+  return t;
+}
+
 template <class T, int D, int ORDER, bool EXACT = false>
 cudaError_t launch_shell(const StageArgs<T>& A, cudaStream_t stream) {
   const int64_t ns = shell_count(D, A.f.m);
   if (ns <= 0) return cudaSuccess;
-  const int threads = 256;
+  const int threads = site_kernel_threads(ns);
   const dim3 grid((unsigned)((ns + threads - 1) / threads));
   if (A.f.ninterior < (int64_t(1) << 31)) k_stage_shell<T, D, ORDER, EXACT, uint32_t><<<grid, threads, 0, stream>>>(A, ns);
   else k_stage_shell<T, D, ORDER, EXACT, uint64_t><<<grid, threads, 0, stream>>>(A, ns);
@@ -131,7 +149,7 @@ cudaError_t launch_shell(const StageArgs<T>& A, cudaStream_t stream) {
 template <class T, int D, int ORDER, bool EXACT = false>
 cudaError_t launch_generic(const StageArgs<T>& A, cudaStream_t stream) {
   if (A.f.ninterior <= 0) return cudaSuccess;
-  const int threads = 256;
+  const int threads = site_kernel_threads(A.f.ninterior);
   const int64_t blocks = (A.f.ninterior + threads - 1) / threads;
   if (A.f.ninterior < (int64_t(1) << 31))
     k_stage_generic<T, D, ORDER, EXACT, uint32_t><<<dim3((unsigned)blocks), threads, 0, stream>>>(A);

@@ -207,6 +207,64 @@ def vortex_rings_3d(n: int = 512, h: float = 0.25, seed: int = 3, R: float = 8.0
                    extra=dict(centres=np.stack([cx, cy, cz], 1)))
 
 
+# Total grid sizes of the timing tables of Sec. 7 (Tables 1-3).
+PAPER_TABLE_SITES = {1: (1000, 10000, 100000, 1000000, 3000000),
+                     2: (961, 10000, 99856, 1000000, 2999824),
+                     3: (9261, 97336, 970299, 2985984)}
+
+
+def paper_timing_problem(dims: int, total: int, order: int = 4) -> Problem:
+    """The timing workloads of Sec. 4 and Sec. 7: s = -1, a = 1, V = 0, MSD
+    walls, k = 0.005 to t = 50 (10,000 steps).
+
+      1D  the dark soliton of Eq. soliton (c = 0.5, Omega = -1) at h = 0.1
+          (the step whose stability bounds Sec. 4 prints), N = total points
+      2D  the dark vortex of Eq. exmp2Dvort with m = 1, its radial profile
+          approximated, as in Sec. 4, by the c = 0 soliton profile
+          tanh(r / sqrt 2); h = 0.25, N = M = floor(sqrt(total))
+      3D  a dark vortex ring of radius d = 5 about the z axis: the 2D m = 1
+          vortex placed at r = d in the r-z half-plane (tanh core, times its
+          mirror at r = -d), h = 3/2, N = M = L = round(cbrt(total)), times
+          the back-flow phase exp(i c z / (2a)) of Eq. 3dvr1.  The paper
+          takes c from an asymptotic formula without printing it; here c is
+          the large-ring speed of Roberts and Grant (1971),
+          U = (ln(8R) - 0.615) / (2R) for i psi_t = -lap psi / 2 + |psi|^2 psi,
+          rescaled to a = 1 (lengths x sqrt(2a)): c = sqrt(2) U(d / sqrt(2)).
+          Without it the ring runs into a wall within the 10,000 steps and
+          the MSD wall ratio diverges.
+    Grids are centred on the origin."""
+    a, s, dt, steps = 1.0, -1.0, 0.005, 10000
+    if dims == 1:
+        h = 0.1
+        x = centred_axis(total, h)
+        return Problem(f"paper_dark_soliton_1d_{total}", (total,), h, a, s, BC_MSD, order,
+                       dark_soliton(x, 0.0), None, steps, dt, extra=dict(x=x))
+    kappa = 1.0 / math.sqrt(2.0)      # sqrt(|Omega| / (2a)) with Omega = -1
+    if dims == 2:
+        n = int(math.isqrt(total))
+        h = 0.25
+        y = centred_axis(n, h)[:, None]
+        x = centred_axis(n, h)[None, :]
+        psi = np.tanh(kappa * np.sqrt(x * x + y * y)) * np.exp(1j * np.arctan2(y, x))
+        return Problem(f"paper_dark_vortex_2d_{n}x{n}", (n, n), h, a, s, BC_MSD, order,
+                       np.ascontiguousarray(psi, dtype=np.complex128), None, steps, dt)
+    n = int(round(total ** (1.0 / 3.0)))
+    h, d = 1.5, 5.0
+    ax = centred_axis(n, h)
+    z = ax[:, None, None]
+    y = ax[None, :, None]
+    x = ax[None, None, :]
+    rc = np.sqrt(x * x + y * y)
+    dp = np.sqrt((rc - d) ** 2 + z * z)
+    dm = np.sqrt((rc + d) ** 2 + z * z)
+    Rs = d / math.sqrt(2.0 * a)
+    c = math.sqrt(2.0 * a) * (math.log(8.0 * Rs) - 0.615) / (2.0 * Rs)
+    psi = np.tanh(kappa * dp) * np.tanh(kappa * dm) * np.exp(1j * (np.arctan2(z, rc - d) - np.arctan2(z, rc + d)))
+    psi = psi * np.exp(1j * c * z / (2.0 * a))
+    return Problem(f"paper_vortex_ring_3d_{n}^3", (n, n, n), h, a, s, BC_MSD, order,
+                   np.ascontiguousarray(psi, dtype=np.complex128), None, steps, dt, extra=dict(c=c))
+
+
 def gaussian_packet_2d(n: int, h: float, A: float, w: float, r0, p, a: float, s: float,
                        omega: float = 0.0):
     """A exp(-|r - r0|^2/(2 w^2)) exp(i p.r) on a centred n x n grid, and the

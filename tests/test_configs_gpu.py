@@ -170,3 +170,31 @@ def test_vortex_rings_512cube_precision_form():
     assert rel_l2(b, a) <= 2e-5
     m64, mmx = g64.mass(), gmx.mass()
     assert abs(mmx - m64) <= 1e-6 * m64
+
+
+@pytest.mark.parametrize("dims,total", [(1, 1000), (1, 10000), (2, 961), (2, 10000), (3, 9261), (3, 97336)])
+@pytest.mark.parametrize("dtype,order", [("c64", 2), ("c128", 4), ("c128", 2), ("c64", 4)])
+def test_paper_timing_workloads_match_oracle(dims, total, dtype, order):
+    """The timing workloads of Sec. 7 at the tables' smaller sizes, 200 steps
+    at k = 0.005, every site against the oracle."""
+    p = W.paper_timing_problem(dims, total, order)
+    n = 200
+    ref = O.rk4(p.psi0, p.h, p.a, p.s, p.dt, n, None, p.bc, order)
+    g = Integrator(p.psi0, p.h, p.a, p.s, None, "msd", order, dtype)
+    g.step(n, p.dt)
+    assert rel_l2(g.numpy(), ref) <= (1e-12 if dtype == "c128" else 2e-5)
+
+
+def test_paper_dark_soliton_full_run():
+    """The 1D timing run of Sec. 7 in full (N = 1000, 10,000 steps to t = 50,
+    2SHOC, FP64): against the oracle, and against the exact moving dark
+    soliton to within the scheme's own error."""
+    p = W.paper_timing_problem(1, 1000, 4)
+    ref = O.rk4(p.psi0, p.h, p.a, p.s, p.dt, p.steps, None, p.bc, 4)
+    exact = W.dark_soliton(p.extra["x"], p.steps * p.dt)
+    g = Integrator(p.psi0, p.h, p.a, p.s, None, "msd", 4, "c128")
+    g.step(p.steps, p.dt)
+    got = g.numpy()
+    assert rel_l2(got, ref) <= 1e-12
+    assert rel_l2(got, exact) <= rel_l2(ref, exact) + 1e-12
+    assert rel_l2(ref, exact) < 1e-3

@@ -221,10 +221,13 @@ def test_autotune_picks_a_tile_and_keeps_results(dtype, tmp_path, monkeypatch):
     psi, V = problem((14, 30, 72), 23)
     h, a, s, order = 0.3, 0.6, -1.0, 4
     dt = stable_dt(psi.shape, h, a, s, order, V)
+    tiled = 2 if dtype == "c128" else 1      # a grid this small defaults to the per-site kernel
     g0 = Integrator(psi, h, a, s, V, "msd", order, dtype)
+    g0.set_kernel(tiled)
     g0.step(6, dt)
     ref = g0.numpy()
     g = Integrator(psi, h, a, s, V, "msd", order, dtype)
+    g.set_kernel(tiled)
     before = g.numpy()
     cfg, ms = g.autotune()
     assert cfg in (0, 1, 2, 3) and ms > 0
@@ -232,9 +235,27 @@ def test_autotune_picks_a_tile_and_keeps_results(dtype, tmp_path, monkeypatch):
     g.step(6, dt)
     assert np.array_equal(ref, g.numpy())
     g2 = Integrator(psi, h, a, s, V, "msd", order, dtype)
+    g2.set_kernel(tiled)
     cfg2, ms2 = g2.autotune()
     assert cfg2 == cfg and ms2 == 0.0                 # served from the cache
     assert (tmp_path / "tune.txt").read_text().count("=") >= 1
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_small_3d_grid_defaults_to_the_per_site_kernel(dtype):
+    """A 3D grid too small for the z-marching kernel's tiles defaults to the
+    one-thread-per-site kernel (nothing for the autotuner to time), with the
+    same result as the tiled kernel of its arithmetic."""
+    psi, V = problem((14, 30, 72), 23)
+    h, a, s, order = 0.3, 0.6, -1.0, 4
+    dt = stable_dt(psi.shape, h, a, s, order, V)
+    g = Integrator(psi, h, a, s, V, "msd", order, dtype)
+    assert g.autotune() == (-1, 0.0)
+    g.step(6, dt)
+    t = Integrator(psi, h, a, s, V, "msd", order, dtype)
+    t.set_kernel(2 if dtype == "c128" else 1)
+    t.step(6, dt)
+    assert np.array_equal(g.numpy(), t.numpy())
 
 
 def test_dt_above_bound_is_rejected():
