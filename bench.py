@@ -52,9 +52,10 @@ ALG_BYTES = {  # dtype -> (with V, without V)
     "c64_acc64": (176, 160),
 }
 # FP64 floating-point operations per site per RK4 step of the FP64 path (FMA = 2):
-# per stage |Psi|^2 (3), N = s|Psi|^2 - V (2), a*Lap = scale x exact integer
-# sum (2), F (4), and the stage update (stage 1: 4, stages 2 and 3: 8,
-# stage 4: 6).  The Laplacian's stencil sums run on the integer pipe.
+# per stage |Psi|^2 (3), N = s|Psi|^2 - V (2), a*Lap = cL x the exact integer
+# sum (2; the kernels fold cL into the stage coefficients, the count keeps the
+# method's multiply), F (4), and the stage update (stage 1: 4, stages 2 and 3:
+# 8, stage 4: 6).  The Laplacian's stencil sums run on the integer pipe.
 FP64_FLOPS_PER_SITE_STEP = 15 + 19 + 19 + 17
 CHUNK = 56   # steps per frame in the end-to-end measurement (the 87x87x203 run's chunk size)
 
