@@ -56,3 +56,27 @@ def test_paper_vortex_ring_3d_core_circle():
     loop = np.concatenate([p.psi0[c - r, c, jr - r:jr + r], p.psi0[c - r:c + r, c, jr + r],
                            p.psi0[c + r, c, jr + r:jr - r:-1], p.psi0[c + r:c - r:-1, c, jr - r]])
     assert abs(_winding(np.angle(loop))) == 1
+
+
+def test_paper_vortex_ring_back_flow_keeps_it_clear_of_the_walls():
+    """Reading of Eq. 3dvr1: with the back-flow c the ring's core stays near
+    z = 0 (without it the ring drifts about 0.5 per unit time into a wall),
+    so the 10,000-step timing run stays finite.  Checked with the oracle over
+    t = 5 on the smallest table grid (21^3)."""
+    import oracle as O
+    p = W.paper_timing_problem(3, 9261, 4)
+    n = p.shape[0]
+    ax = W.centred_axis(n, p.h)
+    z = ax[:, None, None]
+    rc = np.sqrt(ax[None, :, None] ** 2 + ax[None, None, :] ** 2)
+    mask = (rc > 1.5) & (rc < 8.5) & (np.abs(z) < 12)
+
+    def zbar(psi):
+        w = np.clip(1 - np.abs(psi) ** 2, 0, None) * mask
+        return float((w * z).sum() / w.sum())
+
+    out = O.rk4(p.psi0, p.h, p.a, p.s, p.dt, 1000, None, p.bc, 4)
+    still = O.rk4(p.psi0 * np.exp(-1j * p.extra["c"] * z / 2), p.h, p.a, p.s, p.dt, 1000, None, p.bc, 4)
+    assert np.all(np.isfinite(out)) and np.max(np.abs(out)) < 1.5
+    assert abs(zbar(out)) < 2.0
+    assert abs(zbar(still)) > 2.0 * abs(zbar(out))
