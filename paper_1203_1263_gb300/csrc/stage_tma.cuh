@@ -65,19 +65,6 @@ __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* tm,
       : "memory");
 }
 
-// Exact-sum accessor over FP64 slots: converts each stencil operand on use.
-template <class T, int D>
-struct SAccXc3 : GAcc<T, D> {
-  const double2* p[5];
-  int w, o;
-  __device__ __forceinline__ SAccXc3(const Field<T>& f_, int64_t c_) : GAcc<T, D>(f_, c_) {}
-  __device__ __forceinline__ int off(int k, int s) const { return k == 1 ? s * w : (k == 2 ? s : 0); }
-  __device__ __forceinline__ longlong2 fx0() const { return fix2(p[2][o], this->f.F); }
-  __device__ __forceinline__ longlong2 fx1(int k, int s) const {
-    return fix2(k == 0 ? p[2 + s][o] : p[2][o + off(k, s)], this->f.F);
-  }
-};
-
 template <int TX, int TY, class C>
 struct TmaGeom {
   static constexpr int W = TX + 4, H = TY + 4, PS = W * H;
@@ -85,7 +72,7 @@ struct TmaGeom {
   static constexpr uint32_t kSlot = (kBytes + 127u) / 128u * 128u;         // 128-byte aligned slots
 };
 
-template <class T, int ORDER, int S, int TX, int TYT, int RY, int P, bool EXACT>
+template <class T, int ORDER, int S, int TX, int TYT, int RY, int P>
 __global__ void __launch_bounds__(TX* TYT) k_stage3d_tma(const StageArgs<T> A, const __grid_constant__ CUtensorMap tm,
                                                         int zc, long long spin_limit, uint32_t extra_tx) {
   using C = typename T::C;
@@ -150,14 +137,14 @@ __global__ void __launch_bounds__(TX* TYT) k_stage3d_tma(const StageArgs<T> A, c
   PointVals<T> pv_next[RY];
 #pragma unroll
   for (int r = 0; r < RY; ++r)
-    if (deep[r]) pv_next[r] = load_point<T, S, EXACT>(A, zb * plane + col[r], with_v);
+    if (deep[r]) pv_next[r] = load_point<T, S>(A, zb * plane + col[r], with_v);
   bool aborted = false;
   for (int z = zb; z < ze; ++z) {
     PointVals<T> pv[RY];
 #pragma unroll
     for (int r = 0; r < RY; ++r) {
       pv[r] = pv_next[r];
-      if (deep[r] && z + 1 < ze) pv_next[r] = load_point<T, S, EXACT>(A, (z + 1) * plane + col[r], with_v);
+      if (deep[r] && z + 1 < ze) pv_next[r] = load_point<T, S>(A, (z + 1) * plane + col[r], with_v);
     }
     late |= !mbar_wait_bounded(smem_u32(bars + wslot), wpar, spin_limit);
     pl[4] = reinterpret_cast<const C*>(slots + wslot * G::kSlot);
@@ -168,27 +155,15 @@ __global__ void __launch_bounds__(TX* TYT) k_stage3d_tma(const StageArgs<T> A, c
       if (!(deep[r] && deep_z) || late) continue;   // wall-shell sites belong to the shell kernel
       const int idx[3] = {z, gy[r], gx};
       const int64_t c = z * plane + col[r];
-      if constexpr (EXACT) {
-        SAccXc3<T, 3> acc(f, c);
+      SAcc3<T> acc;
 #pragma unroll
-        for (int d = 0; d < 5; ++d) acc.p[d] = reinterpret_cast<const double2*>(pl[d]);
-        acc.w = G::W;
-        acc.o = o[r];
-        const auto pc = acc.at0();
-        const R Nc = fma(f.sG, norm2(pc), -pv[r].v);   // units of cLF (pv holds V / cLF)
-        const auto aL = a_lap_exact_deep<T, 3, ORDER>(f, acc, idx, c, pc, Nc);
-        rk_apply<T, S>(A, c, {-fma(Nc, pc.y, aL.y), fma(Nc, pc.x, aL.x)}, pv[r]);
-      } else {
-        SAcc3<T> acc;
-#pragma unroll
-        for (int d = 0; d < 5; ++d) acc.p[d] = pl[d];
-        acc.w = G::W;
-        acc.o = o[r];
-        const auto pc = acc.at0();
-        const R Nc = fma(f.s, norm2(pc), -pv[r].v);
-        const auto aL = a_lap_body<T, 3, ORDER, SAcc3<T>, false>(f, acc, idx, c, pc, Nc);
-        rk_apply<T, S>(A, c, {-fma(Nc, pc.y, aL.y), fma(Nc, pc.x, aL.x)}, pv[r]);
-      }
+      for (int d = 0; d < 5; ++d) acc.p[d] = pl[d];
+      acc.w = G::W;
+      acc.o = o[r];
+      const auto pc = acc.at0();
+      const R Nc = fma(f.s, norm2(pc), -pv[r].v);
+      const auto aL = a_lap_body<T, 3, ORDER, SAcc3<T>, false>(f, acc, idx, c, pc, Nc);
+      rk_apply<T, S>(A, c, {-fma(Nc, pc.y, aL.y), fma(Nc, pc.x, aL.x)}, pv[r]);
     }
     if (__syncthreads_or(late)) {   // uniform decision: some copy never landed
       aborted = true;
@@ -408,7 +383,7 @@ cudaError_t launch3d_tma_exact_shape(const StageArgs<T>& A, const CUtensorMap* t
   return cudaGetLastError();
 }
 
-template <class T, int ORDER, int S, int TX, int TYT, int RY, int P, bool EXACT>
+template <class T, int ORDER, int S, int TX, int TYT, int RY, int P>
 cudaError_t launch3d_tma_shape(const StageArgs<T>& A, const CUtensorMap* tm, long long spin_limit,
                                uint32_t extra_tx, cudaStream_t stream) {
   constexpr int TY = TYT * RY;
@@ -422,7 +397,7 @@ cudaError_t launch3d_tma_shape(const StageArgs<T>& A, const CUtensorMap* tm, lon
   const int zc = (planes + nzc - 1) / nzc;
   nzc = (planes + zc - 1) / zc;
   const size_t smem = (5 + P) * G::kSlot + (5 + P) * sizeof(uint64_t);
-  auto kern = k_stage3d_tma<T, ORDER, S, TX, TYT, RY, P, EXACT>;
+  auto kern = k_stage3d_tma<T, ORDER, S, TX, TYT, RY, P>;
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -442,12 +417,13 @@ cudaError_t launch3d_tma_stage(const StageArgs<T>& A, const LaunchCfg& L, cudaSt
       case 3: return launch3d_tma_exact_shape<T, ORDER, S, 64, 4, 2, 2>(A, tm, L.spin_limit, L.extra_tx, stream);
       default: return launch3d_tma_exact_shape<T, ORDER, S, 32, 8, 1, 2>(A, tm, L.spin_limit, L.extra_tx, stream);
     }
-  }
-  switch (L.tile_cfg) {   // the tile shapes of tma_tile_shape()
-    case 1: return launch3d_tma_shape<T, ORDER, S, 64, 4, 1, 2, EXACT>(A, tm, L.spin_limit, L.extra_tx, stream);
-    case 2: return launch3d_tma_shape<T, ORDER, S, 32, 8, 2, 2, EXACT>(A, tm, L.spin_limit, L.extra_tx, stream);
-    case 3: return launch3d_tma_shape<T, ORDER, S, 64, 4, 2, 2, EXACT>(A, tm, L.spin_limit, L.extra_tx, stream);
-    default: return launch3d_tma_shape<T, ORDER, S, 32, 8, 1, 2, EXACT>(A, tm, L.spin_limit, L.extra_tx, stream);
+  } else {
+    switch (L.tile_cfg) {   // the tile shapes of tma_tile_shape()
+      case 1: return launch3d_tma_shape<T, ORDER, S, 64, 4, 1, 2>(A, tm, L.spin_limit, L.extra_tx, stream);
+      case 2: return launch3d_tma_shape<T, ORDER, S, 32, 8, 2, 2>(A, tm, L.spin_limit, L.extra_tx, stream);
+      case 3: return launch3d_tma_shape<T, ORDER, S, 64, 4, 2, 2>(A, tm, L.spin_limit, L.extra_tx, stream);
+      default: return launch3d_tma_shape<T, ORDER, S, 32, 8, 1, 2>(A, tm, L.spin_limit, L.extra_tx, stream);
+    }
   }
 }
 
