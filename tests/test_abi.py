@@ -65,3 +65,24 @@ def test_create_rejects_bad_arguments_before_touching_the_gpu(args, code):
     assert rc == code
     assert ctx.value is None
     assert lib.nlse_last_error()
+
+
+def _run(**kw):
+    d = L.RunDesc()
+    d.n[0], d.n[1] = kw.get("n", (64, 80))
+    d.h, d.a, d.s = kw.get("h", 0.25), kw.get("a", 0.7), kw.get("s", -1.0)
+    d.dt, d.bc, d.order = kw.get("dt", 0.005), kw.get("bc", L.BC_MSD), kw.get("order", 4)
+    d.psi, d.V = kw.get("psi", 4096), None
+    return d
+
+
+@pytest.mark.parametrize("bc", [L.BC_DIRICHLET, L.BC_MSD, L.BC_L0])
+def test_batch_workspace_accepts_every_boundary(bc):
+    runs = (L.RunDesc * 2)(_run(bc=bc), _run(n=(33, 17), order=2, bc=bc))
+    assert L.lib().nlse_batch_workspace_bytes(2, runs) >= 2 * (64 * 80 + 33 * 17) * 8
+
+
+@pytest.mark.parametrize("bad", [dict(bc=3), dict(order=3), dict(n=(2, 40)), dict(h=0.0), dict(dt=1.0), dict(psi=4100)])
+def test_batch_workspace_rejects_bad_runs(bad):
+    runs = (L.RunDesc * 2)(_run(), _run(**bad))
+    assert L.lib().nlse_batch_workspace_bytes(2, runs) == 0
