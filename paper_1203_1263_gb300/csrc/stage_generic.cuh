@@ -1,7 +1,8 @@
 // Generic stage kernel: one thread per interior site, all reads through the
 // read-only cache.  Simple and dimension-agnostic; it is the correctness
-// baseline that the tiled kernels are checked against, and the kernel used
-// for 1D grids.
+// baseline that the tiled kernels are checked against, the kernel used for
+// 1D grids, and the default for 3D grids too small to fill the GPU with the
+// z-marching kernel's tiles (latency, not bandwidth, bounds those).
 #pragma once
 #include "nlse_device.cuh"
 
