@@ -169,9 +169,10 @@ def test_tiled_kernel_equals_generic_bitwise(dtype, dims, shape, tile_cfg):
             assert np.array_equal(res[2], res[3]), (order, bc)
 
 
+@pytest.mark.parametrize("bc", ["dirichlet", "l0"])
 @pytest.mark.parametrize("variant", [2, 3])
 @pytest.mark.parametrize("dims,shape", [(2, (19, 45)), (3, (9, 21, 70))])
-def test_exact_sum_out_of_range_falls_back(variant, dims, shape):
+def test_exact_sum_out_of_range_falls_back(variant, dims, shape, bc):
     """The exact-sum stencil fixes its range from Psi at creation; a state
     scaled far beyond it afterwards must still integrate correctly (every
     out-of-range site takes the FP64 stencil)."""
@@ -179,11 +180,11 @@ def test_exact_sum_out_of_range_falls_back(variant, dims, shape):
     h, a, s, order = 0.3, 0.6, -1.0, 4
     big = 100.0 * psi
     dt = 0.2 * O.stability_bound(dims, h, a, order, float(np.max(V)), abs(s) * 1.7e4)
-    g = Integrator(psi, h, a, s, V, "dirichlet", order, "c128")
+    g = Integrator(psi, h, a, s, V, bc, order, "c128")
     g.set_kernel(variant)
     g.psi.copy_(torch.from_numpy(big).to(g.psi.device))
     g.step(4, dt)
-    ref = O.rk4(big, h, a, s, dt, 4, V, W.BC_DIRICHLET, order)
+    ref = O.rk4(big, h, a, s, dt, 4, V, BCS[bc], order)
     compare(g.numpy(), ref, "c128")
 
 
