@@ -13,7 +13,8 @@ directly with numpy, channels-last, zero padding:
 with o_t = (t // 3 - 1, t % 3 - 1), and its gradient by the chain rule
 (backward-data is the transpose convolution with the offsets negated;
 silu'(z) = s (1 + z (1 - s)), s = sigmoid(z)).  Parity status: pinned by
-central finite differences of the loss (tests/test_surrogate_ref.py).
+central finite differences of the loss, and the forward convolution by
+scipy's 2D correlation with the dilated taps (tests/test_surrogate_ref.py).
 Parameter layout: per layer W [cout][9][cin] then b [cout].
 """
 import numpy as np

@@ -46,3 +46,51 @@ def test_tap_convention_is_a_shift():
     z = S.conv(h, Wl, np.zeros(2), 1)
     assert np.array_equal(z[0, :, :-1, 0], x.real[0, :, 1:])
     assert np.all(z[0, :, -1, :] == 0)
+
+
+def test_conv_equals_scipy_correlation_with_a_dilated_kernel():
+    """A dilated 3x3 convolution with zero padding is scipy's 2D correlation
+    ('same', zero fill) with the taps spread onto a (2d+1)^2 grid."""
+    signal = __import__("pytest").importorskip("scipy.signal")
+    rng = np.random.default_rng(11)
+    nb, H, Wd, ci, co = 2, 9, 11, 3, 2
+    x = rng.standard_normal((nb, H, Wd, ci))
+    Wl = rng.standard_normal((co, 9, ci))
+    bl = rng.standard_normal(co)
+    for d in (1, 2, 3):
+        z = S.conv(x, Wl, bl, d)
+        for o in range(co):
+            k = np.zeros((2 * d + 1, 2 * d + 1, ci))
+            for t in range(9):
+                k[d + d * (t // 3 - 1), d + d * (t % 3 - 1), :] = Wl[o, t, :]
+            for n in range(nb):
+                ref = bl[o] + sum(signal.correlate2d(x[n, :, :, c], k[:, :, c], mode="same", boundary="fill")
+                                  for c in range(ci))
+                assert np.allclose(z[n, :, :, o], ref, rtol=1e-12, atol=1e-12)
+
+
+def test_single_layer_network_is_one_correlation_of_the_features():
+    """layers = 1: psi_out = psi + z0 + i z1 with z the dilated correlation of
+    the four input features (Re, Im, |psi|^2 Re, |psi|^2 Im) of psi."""
+    signal = __import__("pytest").importorskip("scipy.signal")
+    shapes = S.layer_shapes(8, 1)
+    assert shapes == [(2, S.N_IN)]
+    rng = np.random.default_rng(12)
+    params = rng.standard_normal(2 * 9 * S.N_IN + 2)
+    psi = W.random_field((1, 7, 8), 13)
+    out, _, _ = S.forward(params, psi, 8, 1, (2,))
+    Wl = params[:2 * 9 * S.N_IN].reshape(2, 9, S.N_IN)
+    b = params[-2:]
+    r = np.abs(psi[0]) ** 2
+    feats = [psi[0].real, psi[0].imag, r * psi[0].real, r * psi[0].imag]
+    d = 2
+    z = []
+    for o in range(2):
+        acc = np.full(psi.shape[1:], b[o])
+        for c in range(S.N_IN):
+            k = np.zeros((2 * d + 1, 2 * d + 1))
+            for t in range(9):
+                k[d + d * (t // 3 - 1), d + d * (t % 3 - 1)] = Wl[o, t, c]
+            acc = acc + signal.correlate2d(feats[c], k, mode="same", boundary="fill")
+        z.append(acc)
+    assert np.allclose(out[0], psi[0] + z[0] + 1j * z[1], rtol=1e-12, atol=1e-12)
