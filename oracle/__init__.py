@@ -9,7 +9,10 @@ returns new arrays; nothing is modified in place.
 Parity status of each function (pins are in tests/test_oracle_pins.py):
   evalF, laplacian, rk4      pinned (closed forms, exact solitons, brute force;
                              the L0 boundary by its pointwise boundary ODE and
-                             multilinear fields in a constant potential)
+                             multilinear fields in a constant potential; the
+                             periodic grid by the discrete Fourier spectrum of
+                             both Laplacians, Fourier modes under RK4, plane
+                             waves of the cubic equation and shift invariance)
   mass                       pinned (closed form, exact-sum comparison)
   energy                     pinned (conservation, closed form for sine modes)
   stability_bound            pinned (numbers printed in Sec. 4 and Sec. 3.4)
@@ -33,6 +36,7 @@ _lib = None
 BC_DIRICHLET = 0
 BC_MSD = 1
 BC_L0 = 2
+BC_PERIODIC = 3
 
 
 def build(force: bool = False) -> str:

@@ -32,6 +32,10 @@
  *     L0:        dPsi_b/dt = i (s|Psi_b|^2 - V_b) Psi_b (Eq. BCL0dt);
  *                D_b = 0 (Eq. BCL0lap).
  *     The boundary D_b enters only the 2SHOC step 2 of interior sites.
+ *   Periodic (not one of the paper's boundary forms; its stability analysis,
+ *   Sec. 3.4, assumes it): the grid has no boundary sites.  Site N[k] along
+ *   axis k is site 0 again (period N[k] h), so every site is interior and
+ *   every neighbour index is taken modulo N[k].
  *
  *   RK4: the ten-step algorithmic form of Sec. 3.1, Eq. RK4, with
  *   K_tot, Psi_tmp and K_tmp held as whole-grid arrays.
@@ -56,6 +60,7 @@
 #define BC_DIRICHLET 0
 #define BC_MSD 1
 #define BC_L0 2
+#define BC_PERIODIC 3
 #define MSD_TINY 1e-300
 
 typedef struct {
@@ -73,6 +78,7 @@ static int setup(grid *g, int d, const int64_t *n, double h, double a, double s,
   if (d < 1 || d > 3) return -1;
   g->d = d;
   g->total = 1;
+  for (int k = 0; k < 3; ++k) { g->n[k] = 1; g->st[k] = 0; }
   for (int k = d - 1; k >= 0; --k) {
     if (n[k] < 3) return -1;
     g->n[k] = n[k];
@@ -80,7 +86,8 @@ static int setup(grid *g, int d, const int64_t *n, double h, double a, double s,
     g->total *= n[k];
   }
   g->h = h; g->a = a; g->s = s; g->V = V; g->bc = bc; g->order = order;
-  if (!(order == 2 || order == 4) || !(bc == BC_DIRICHLET || bc == BC_MSD || bc == BC_L0)) return -1;
+  if (!(order == 2 || order == 4)) return -1;
+  if (!(bc == BC_DIRICHLET || bc == BC_MSD || bc == BC_L0 || bc == BC_PERIODIC)) return -1;
   return 0;
 }
 
@@ -90,6 +97,7 @@ static void decode(const grid *g, int64_t p, int64_t idx[3]) {
 
 static int is_boundary(const grid *g, int64_t p) {
   int64_t idx[3];
+  if (g->bc == BC_PERIODIC) return 0;
   decode(g, p, idx);
   for (int k = 0; k < g->d; ++k)
     if (idx[k] == 0 || idx[k] == g->n[k] - 1) return 1;
@@ -105,6 +113,23 @@ static int64_t inward(const grid *g, int64_t p) {
     else if (idx[k] == g->n[k] - 1) q -= g->st[k];
   }
   return q;
+}
+
+/* The site o = (o0, o1, o2) cells away from p (o_k along axis k).  On a
+ * periodic grid each index wraps modulo N[k]; otherwise the caller only asks
+ * for sites inside the grid (interior p, |o_k| <= 1). */
+static int64_t nb(const grid *g, int64_t p, int o0, int o1, int o2) {
+  const int o[3] = {o0, o1, o2};
+  if (g->bc != BC_PERIODIC) return p + o0 * g->st[0] + o1 * g->st[1] + o2 * g->st[2];
+  int64_t idx[3], q = 0;
+  decode(g, p, idx);
+  for (int k = 0; k < g->d; ++k) q += ((idx[k] + o[k] + g->n[k]) % g->n[k]) * g->st[k];
+  return q;
+}
+
+/* the site one cell away from p along axis k, in direction s (+1 or -1) */
+static int64_t nb1(const grid *g, int64_t p, int k, int s) {
+  return nb(g, p, k == 0 ? s : 0, k == 1 ? s : 0, k == 2 ? s : 0);
 }
 
 static double Vat(const grid *g, int64_t p) { return g->V ? g->V[p] : 0.0; }
@@ -124,7 +149,7 @@ static void compute_D_interior(const grid *g, const double *psi, double *D) {
     if (is_boundary(g, p)) { D[2 * p] = D[2 * p + 1] = 0.0; continue; }
     for (int c = 0; c < 2; ++c) {
       double sum = 0.0;
-      for (int k = 0; k < g->d; ++k) sum += psi[2 * (p + g->st[k]) + c] + psi[2 * (p - g->st[k]) + c];
+      for (int k = 0; k < g->d; ++k) sum += psi[2 * nb1(g, p, k, 1) + c] + psi[2 * nb1(g, p, k, -1) + c];
       sum += -2.0 * g->d * psi[2 * p + c];
       D[2 * p + c] = inv_h2 * sum;
     }
@@ -168,37 +193,36 @@ static void compute_D(const grid *g, const double *psi, double *D) {
 /* ---- Step 2: the Laplacian at interior sites ---- */
 static void compute_L(const grid *g, const double *psi, const double *D, double *L) {
   const double inv_h2 = 1.0 / (g->h * g->h);
-  const int64_t *st = g->st;
 #pragma omp parallel for schedule(static)
   for (int64_t p = 0; p < g->total; ++p) {
     if (is_boundary(g, p)) { L[2 * p] = L[2 * p + 1] = 0.0; continue; }
     for (int c = 0; c < 2; ++c) {
-#define PS(off) psi[2 * (p + (off)) + c]
-#define DD(off) D[2 * (p + (off)) + c]
+/* Psi and D at the site (o0, o1, o2) cells away from p */
+#define PS(o0, o1, o2) psi[2 * nb(g, p, o0, o1, o2) + c]
+#define DD(o0, o1, o2) D[2 * nb(g, p, o0, o1, o2) + c]
       double v;
       if (g->order == 2) {
-        v = DD(0);
+        v = DD(0, 0, 0);
       } else if (g->d == 1) {
         /* Eq. 2shoc1d2: (7/6) D_i - (1/12)(D_{i+1} + D_{i-1}) */
-        v = (7.0 / 6.0) * DD(0) - (1.0 / 12.0) * (DD(st[0]) + DD(-st[0]));
+        v = (7.0 / 6.0) * DD(0, 0, 0) - (1.0 / 12.0) * (DD(1, 0, 0) + DD(-1, 0, 0));
       } else if (g->d == 2) {
         /* Eq. 2d2shocs2: -(1/12)[plus stencil, centre -12] D + (1/(6h^2))[corners 1, centre -4] Psi */
-        const int64_t a0 = st[0], a1 = st[1];
-        double sd = DD(a0) + DD(-a0) + DD(a1) + DD(-a1) - 12.0 * DD(0);
-        double sp = PS(a0 + a1) + PS(a0 - a1) + PS(-a0 + a1) + PS(-a0 - a1) - 4.0 * PS(0);
+        double sd = DD(1, 0, 0) + DD(-1, 0, 0) + DD(0, 1, 0) + DD(0, -1, 0) - 12.0 * DD(0, 0, 0);
+        double sp = PS(1, 1, 0) + PS(1, -1, 0) + PS(-1, 1, 0) + PS(-1, -1, 0) - 4.0 * PS(0, 0, 0);
         v = -(1.0 / 12.0) * sd + (inv_h2 / 6.0) * sp;
       } else {
         /* Eq. 3d2shocs2: -(1/12)[6 face neighbours, centre -10] D
          *                + (1/(6h^2))[12 edge-diagonal neighbours, centre -12] Psi */
-        const int64_t a0 = st[0], a1 = st[1], a2 = st[2];
-        double sd = DD(a0) + DD(-a0) + DD(a1) + DD(-a1) + DD(a2) + DD(-a2) - 10.0 * DD(0);
+        double sd = DD(1, 0, 0) + DD(-1, 0, 0) + DD(0, 1, 0) + DD(0, -1, 0) + DD(0, 0, 1) + DD(0, 0, -1) -
+                    10.0 * DD(0, 0, 0);
         double sp = 0.0;
         /* plane j+1 and j-1 (axis 0 = j here): the four in-plane face neighbours */
-        sp += PS(a0 + a1) + PS(a0 - a1) + PS(a0 + a2) + PS(a0 - a2);
-        sp += PS(-a0 + a1) + PS(-a0 - a1) + PS(-a0 + a2) + PS(-a0 - a2);
+        sp += PS(1, 1, 0) + PS(1, -1, 0) + PS(1, 0, 1) + PS(1, 0, -1);
+        sp += PS(-1, 1, 0) + PS(-1, -1, 0) + PS(-1, 0, 1) + PS(-1, 0, -1);
         /* plane j: the four corners */
-        sp += PS(a1 + a2) + PS(a1 - a2) + PS(-a1 + a2) + PS(-a1 - a2);
-        sp += -12.0 * PS(0);
+        sp += PS(0, 1, 1) + PS(0, 1, -1) + PS(0, -1, 1) + PS(0, -1, -1);
+        sp += -12.0 * PS(0, 0, 0);
         v = -(1.0 / 12.0) * sd + (inv_h2 / 6.0) * sp;
       }
       L[2 * p + c] = v;

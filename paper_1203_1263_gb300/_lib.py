@@ -23,6 +23,7 @@ NLSE_ESTATE = -7
 BC_DIRICHLET = 0
 BC_MSD = 1
 BC_L0 = 2
+BC_PERIODIC = 3
 C128 = 0
 C64 = 1
 C64_ACC64 = 2

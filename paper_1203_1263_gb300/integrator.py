@@ -15,7 +15,7 @@ import torch
 from . import _lib as L
 
 _DTYPES = {"c128": L.C128, "c64": L.C64, "c64_acc64": L.C64_ACC64}
-_BCS = {"dirichlet": L.BC_DIRICHLET, "msd": L.BC_MSD, "l0": L.BC_L0}
+_BCS = {"dirichlet": L.BC_DIRICHLET, "msd": L.BC_MSD, "l0": L.BC_L0, "periodic": L.BC_PERIODIC}
 
 
 def _code(table, v):

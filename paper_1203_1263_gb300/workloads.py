@@ -24,6 +24,7 @@ import numpy as np
 BC_DIRICHLET = 0
 BC_MSD = 1
 BC_L0 = 2
+BC_PERIODIC = 3
 
 _GAMMA = np.uint64(0x9E3779B97F4A7C15)
 _M1 = np.uint64(0xBF58476D1CE4E5B9)

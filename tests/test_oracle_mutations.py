@@ -19,14 +19,14 @@ PINS = "tests/test_oracle_pins.py::"
 # name: (text in nlse_oracle.c, replacement, pin that must fail)
 MUTATIONS = {
     "3d_edge_term_dropped": (
-        "sp += PS(a1 + a2) + PS(a1 - a2) + PS(-a1 + a2) + PS(-a1 - a2);",
-        "sp += PS(a1 + a2) + PS(a1 - a2) + PS(-a1 + a2);",
+        "sp += PS(0, 1, 1) + PS(0, 1, -1) + PS(0, -1, 1) + PS(0, -1, -1);",
+        "sp += PS(0, 1, 1) + PS(0, 1, -1) + PS(0, -1, 1);",
         "test_stationary_dark_soliton_dirichlet[3-2-4-4.0-0.35]"),
     "2d_centre_coefficient": (
-        "- 12.0 * DD(0);", "- 11.0 * DD(0);",
+        "- 12.0 * DD(0, 0, 0);", "- 11.0 * DD(0, 0, 0);",
         "test_stationary_dark_soliton_dirichlet[2-0-4-4.0-0.35]"),
     "1d_2shoc_coefficient": (
-        "(7.0 / 6.0) * DD(0)", "(7.0 / 6.1) * DD(0)",
+        "(7.0 / 6.0) * DD(0, 0, 0)", "(7.0 / 6.1) * DD(0, 0, 0)",
         "test_bright_soliton_convergence[4-4.0-0.3]"),
     "msd_inward_index": (
         "if (idx[k] == 0) q += g->st[k];", "if (idx[k] == 0) q -= 0;",
@@ -81,6 +81,17 @@ MUTATIONS = {
         "} else if (g->bc == BC_L0) {\n      D[2 * p] = 0.0;",
         "} else if (g->bc == BC_L0) {\n      D[2 * p] = -(1.0 / g->a) * Nat(g, psi, p) * re;",
         "test_l0_harmonic_field_in_constant_potential[4-shape0]"),
+    "periodic_wrap_modulus": (
+        "q += ((idx[k] + o[k] + g->n[k]) % g->n[k]) * g->st[k];",
+        "q += ((idx[k] + o[k] + g->n[k]) % (g->n[k] - 1)) * g->st[k];",
+        "test_periodic_laplacian_is_its_fourier_symbol[2-shape2]"),
+    "periodic_wrap_wrong_axis": (
+        "q += ((idx[k] + o[k] + g->n[k]) % g->n[k]) * g->st[k];",
+        "q += ((idx[k] + o[0] + g->n[k]) % g->n[k]) * g->st[k];",
+        "test_periodic_fourier_modes_exact_rk4[4-shape3-modes3]"),
+    "periodic_has_boundary_sites": (
+        "  if (g->bc == BC_PERIODIC) return 0;\n", "",
+        "test_periodic_laplacian_is_its_fourier_symbol[4-shape3]"),
 }
 
 

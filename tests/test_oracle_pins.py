@@ -505,13 +505,140 @@ def test_vortex_rotation_symmetry():
     assert np.max(np.abs(out - p.psi0)) > 1e-3      # it did evolve
 
 
-@pytest.mark.parametrize("bc", [W.BC_DIRICHLET, W.BC_MSD, W.BC_L0])
+@pytest.mark.parametrize("bc", [W.BC_DIRICHLET, W.BC_MSD, W.BC_L0, W.BC_PERIODIC])
 def test_split_continuation_bitwise(bc):
     psi = W.random_field((9, 10), seed=31)
     V = W.random_potential((9, 10), seed=32)
     a1 = O.rk4(psi, 0.3, 0.8, 1.0, 0.002, 7, V, bc, 4)
     a2 = O.rk4(O.rk4(psi, 0.3, 0.8, 1.0, 0.002, 3, V, bc, 4), 0.3, 0.8, 1.0, 0.002, 4, V, bc, 4)
     assert np.array_equal(a1, a2)
+
+
+# ---------------------------------------------------------------------------
+# Periodic grids (the boundary of the stability analysis, Sec. 3.4): no
+# boundary sites, every neighbour index taken modulo N.  Pinned by the
+# discrete Fourier spectrum of both Laplacians (numpy's FFT), exact Fourier
+# modes under RK4, plane waves of the cubic equation, shift invariance and
+# closed-form mass and energy.
+# ---------------------------------------------------------------------------
+
+PERIODIC_SHAPES = [(16,), (9,), (8, 10), (7, 5), (6, 7, 5), (4, 6, 8)]
+
+
+def fourier_symbol(shape, h, order):
+    """lambda(k) of the periodic CD (order 2) or 2SHOC (order 4) Laplacian on
+    the grid's discrete Fourier modes: sum_alpha sigma_alpha, or
+    sum_alpha (sigma_alpha - h^2 sigma_alpha^2 / 12), sigma = -(4/h^2) sin^2(theta/2)."""
+    lam = np.zeros(shape)
+    for ax, n in enumerate(shape):
+        theta = 2.0 * np.pi * np.fft.fftfreq(n)
+        sig = -(4.0 / (h * h)) * np.sin(theta / 2) ** 2
+        term = sig if order == 2 else sig - h * h * sig * sig / 12.0
+        sh = [1] * len(shape)
+        sh[ax] = n
+        lam = lam + term.reshape(sh)
+    return lam
+
+
+@pytest.mark.parametrize("shape", PERIODIC_SHAPES)
+@pytest.mark.parametrize("order", [2, 4])
+def test_periodic_laplacian_is_its_fourier_symbol(shape, order):
+    """On a random field, D (step 1) is the CD symbol and Lap the scheme's symbol, applied by FFT."""
+    h = 0.3
+    psi = W.random_field(shape, seed=61 + len(shape))
+    D, L = O.laplacian(psi, h, 1.0, 0.0, None, W.BC_PERIODIC, order)
+    fpsi = np.fft.fftn(psi)
+    D_ref = np.fft.ifftn(fpsi * fourier_symbol(shape, h, 2))
+    L_ref = np.fft.ifftn(fpsi * fourier_symbol(shape, h, order))
+    scale = np.max(np.abs(L_ref))
+    assert np.max(np.abs(D - D_ref)) < 1e-12 * scale
+    assert np.max(np.abs(L - L_ref)) < 1e-12 * scale
+
+
+def fourier_mode(shape, modes):
+    """exp(i sum_alpha 2 pi m_alpha i_alpha / N_alpha)."""
+    out = np.ones(shape, dtype=np.complex128)
+    for ax, (n, m) in enumerate(zip(shape, modes)):
+        v = np.exp(2j * np.pi * m * np.arange(n) / n)
+        sh = [1] * len(shape)
+        sh[ax] = n
+        out = out * v.reshape(sh)
+    return out
+
+
+FOURIER_CASES = [((16,), (8,)), ((9,), (2,)), ((8, 10), (3, 5)), ((6, 7, 5), (1, 3, 2)), ((4, 6, 8), (2, 3, 4))]
+
+
+@pytest.mark.parametrize("shape,modes", FOURIER_CASES)
+@pytest.mark.parametrize("order", [2, 4])
+def test_periodic_fourier_modes_exact_rk4(shape, modes, order):
+    """s = 0, V = 0: a Fourier mode (Nyquist included) is multiplied by R(i a dt lambda) per step."""
+    h, a, dt, n = 0.3, 0.7, 0.004, 25
+    psi0 = fourier_mode(shape, modes)
+    lam = fourier_symbol(shape, h, order)[tuple(m % N for m, N in zip(modes, shape))]
+    out = O.rk4(psi0, h, a, 0.0, dt, n, None, W.BC_PERIODIC, order)
+    assert rel_l2(out, rk4_amplification(1j * a * dt * lam) ** n * psi0) < 1e-13
+
+
+@pytest.mark.parametrize("shape,modes", FOURIER_CASES[1:4])
+@pytest.mark.parametrize("order", [2, 4])
+def test_periodic_plane_wave_of_the_cubic_equation(shape, modes, order):
+    """|Psi| is the same at every site of a plane wave, so each site is the
+    scalar RK4 iterate of z' = i(a lambda + s|z|^2 - V0) z times the wave's phase."""
+    h, a, s, V0, A, dt, n = 0.3, 0.7, -1.3, 0.4, 1.2, 0.003, 30
+    phase = fourier_mode(shape, modes)
+    lam = fourier_symbol(shape, h, order)[tuple(m % N for m, N in zip(modes, shape))]
+    V = np.full(shape, V0)
+    out = O.rk4(A * phase, h, a, s, dt, n, V, W.BC_PERIODIC, order)
+    f = lambda z: 1j * (a * lam + s * abs(z) ** 2 - V0) * z
+    z = complex(A)
+    for _ in range(n):
+        k1 = f(z); k2 = f(z + dt / 2 * k1); k3 = f(z + dt / 2 * k2); k4 = f(z + dt * k3)
+        z = z + dt / 6 * (k1 + 2 * k2 + 2 * k3 + k4)
+    assert np.max(np.abs(out - z * phase)) < 1e-13 * A
+
+
+@pytest.mark.parametrize("shape", [(11,), (6, 9), (5, 4, 7)])
+@pytest.mark.parametrize("order", [2, 4])
+def test_periodic_grid_is_shift_invariant(shape, order):
+    """A periodic grid has no distinguished site: shifting the state and the
+    potential by any number of cells along any axis shifts the result, bit for bit."""
+    psi = W.random_field(shape, seed=71)
+    V = W.random_potential(shape, seed=72)
+    out = O.rk4(psi, 0.4, 0.9, 1.1, 0.003, 6, V, W.BC_PERIODIC, order)
+    for ax in range(len(shape)):
+        for k in (1, 3):
+            got = O.rk4(np.roll(psi, k, ax), 0.4, 0.9, 1.1, 0.003, 6, np.roll(V, k, ax), W.BC_PERIODIC, order)
+            assert np.array_equal(got, np.roll(out, k, ax)), (ax, k)
+
+
+@pytest.mark.parametrize("order", [2, 4])
+def test_periodic_mass_and_energy_closed_form(order):
+    """Every site of a plane wave counts (no boundary): M = h^d N A^2 and
+    E = h^d N [-a lambda A^2 + V0 A^2 - (s/2) A^4]."""
+    shape, modes, h, a, s, V0, A = (6, 7, 5), (1, 3, 2), 0.3, 0.7, -1.3, 0.4, 1.2
+    psi = A * fourier_mode(shape, modes)
+    lam = fourier_symbol(shape, h, order)[modes]
+    n = np.prod(shape)
+    assert abs(O.mass(psi, h) - h ** 3 * n * A * A) < 1e-13 * h ** 3 * n * A * A
+    e = O.energy(psi, h, a, s, np.full(shape, V0), W.BC_PERIODIC, order)
+    e_ref = h ** 3 * n * (-a * lam * A * A + V0 * A * A - 0.5 * s * A ** 4)
+    assert abs(e - e_ref) < 1e-12 * abs(e_ref)
+
+
+@pytest.mark.parametrize("order", [2, 4])
+def test_periodic_linear_mass_nonincreasing(order):
+    """RK4 on the imaginary axis has |R(iy)| <= 1 up to the bound, so the free
+    linear flow on a periodic grid can only lose mass."""
+    psi = W.random_field((12, 10), seed=81)
+    h, a = 0.3, 1.0
+    dt = 0.9 * O.stability_bound(2, h, a, order)
+    m = [O.mass(psi, h)]
+    for _ in range(5):
+        psi = O.rk4(psi, h, a, 0.0, dt, 4, None, W.BC_PERIODIC, order)
+        m.append(O.mass(psi, h))
+    assert all(m[i + 1] <= m[i] * (1 + 1e-14) for i in range(5))
+    assert m[-1] < m[0] * (1 - 1e-6)
 
 
 def test_bad_arguments_rejected():
