@@ -8,13 +8,17 @@ directly with numpy, channels-last, zero padding:
     h_l = z_l * sigmoid(z_l)                       (l < L-1)
     psi_out = psi_in + z_{L-1}[.., 0] + i z_{L-1}[.., 1]
     loss = mean over all real components of (psi_out - target)^2
+           + mass_weight * mean over states of ((M(psi_out) - M(target)) / M(target))^2,
+           M(x) = sum over the state's sites of |x|^2
     optional mass projection (inference only): psi_out * sqrt(M_in / M_out)
 
 with o_t = (t // 3 - 1, t % 3 - 1), and its gradient by the chain rule
 (backward-data is the transpose convolution with the offsets negated;
 silu'(z) = s (1 + z (1 - s)), s = sigmoid(z)).  Parity status: pinned by
-central finite differences of the loss, and the forward convolution by
-scipy's 2D correlation with the dilated taps (tests/test_surrogate_ref.py).
+central finite differences of the loss (with and without the mass term), the
+mass term's closed form on a bias-only network, the forward convolution by
+scipy's 2D correlation with the dilated taps, and the mass projection by its
+closed form on scaled states (tests/test_surrogate_ref.py).
 Parameter layout: per layer W [cout][9][cin] then b [cout].
 """
 import numpy as np
@@ -75,13 +79,22 @@ def forward(params, psi, channels, layers, dilations):
     return psi + y[..., 0] + 1j * y[..., 1], hs, zs
 
 
-def loss_and_grad(params, psi, target, channels, layers, dilations):
+def loss_and_grad(params, psi, target, channels, layers, dilations, mass_weight=0.0):
     Ws, bs = unpack(params, channels, layers)
     out, hs, zs = forward(params, psi, channels, layers, dilations)
     e = np.stack([(out - target).real, (out - target).imag], axis=-1)
     count = e.size
     loss = float(np.sum(e * e) / count)
     dz = 2.0 * e / count                       # d loss / d z_{L-1}
+    if mass_weight:
+        # the mass term: d/d out of mean_b delta_b^2 is (2 delta_b / nb) (2 out / M_t,b)
+        nb = psi.shape[0]
+        m_out = np.sum(np.abs(out) ** 2, axis=(1, 2))
+        m_t = np.sum(np.abs(target) ** 2, axis=(1, 2))
+        delta = (m_out - m_t) / m_t
+        loss += float(mass_weight * np.mean(delta * delta))
+        coef = mass_weight * 4.0 * delta / (nb * m_t)
+        dz = dz + coef[:, None, None, None] * np.stack([out.real, out.imag], axis=-1)
     grads = [None] * layers
     for l in range(layers - 1, -1, -1):
         x, d = hs[l], dilations[l]

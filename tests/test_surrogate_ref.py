@@ -1,6 +1,7 @@
 """Pins of the FP64 surrogate reference (CPU): central finite differences of
 the loss, and closed-form cases of the network definition."""
 import numpy as np
+import pytest
 
 from oracle import surrogate_ref as S
 from paper_1203_1263_gb300 import workloads as W
@@ -14,9 +15,10 @@ def _problem(C=3, L=3, dil=(1, 2, 1), shape=(2, 6, 7), seed=3):
     return params, psi, target, C, L, dil
 
 
-def test_gradient_matches_finite_differences():
+@pytest.mark.parametrize("mass_weight", [0.0, 0.7])
+def test_gradient_matches_finite_differences(mass_weight):
     params, psi, target, C, L, dil = _problem()
-    loss, g = S.loss_and_grad(params, psi, target, C, L, dil)
+    loss, g = S.loss_and_grad(params, psi, target, C, L, dil, mass_weight)
     eps = 1e-6
     rng = np.random.default_rng(0)
     idx = rng.choice(params.size, 60, replace=False)
@@ -24,8 +26,41 @@ def test_gradient_matches_finite_differences():
         p1, p2 = params.copy(), params.copy()
         p1[i] += eps
         p2[i] -= eps
-        fd = (S.loss_and_grad(p1, psi, target, C, L, dil)[0] - S.loss_and_grad(p2, psi, target, C, L, dil)[0]) / (2 * eps)
+        fd = (S.loss_and_grad(p1, psi, target, C, L, dil, mass_weight)[0] -
+              S.loss_and_grad(p2, psi, target, C, L, dil, mass_weight)[0]) / (2 * eps)
         assert abs(fd - g[i]) <= 1e-6 * max(1.0, abs(fd)), (i, fd, g[i])
+
+
+def test_mass_term_closed_form_on_a_bias_only_network():
+    """A network whose only non-zero parameter is the output bias b0 (real)
+    maps psi to psi + b0 at every site, so with target = psi the MSE is b0^2/2
+    and each state's relative mass change is (2 b0 sum Re psi + b0^2 HW) / M."""
+    params, psi, _, C, L, dil = _problem()
+    params[:] = 0.0
+    b0 = 0.125
+    params[-2] = b0
+    mu = 3.0
+    loss, _ = S.loss_and_grad(params, psi, psi, C, L, dil, mu)
+    hw = psi.shape[1] * psi.shape[2]
+    m = np.sum(np.abs(psi) ** 2, axis=(1, 2))
+    delta = (2 * b0 * np.sum(psi.real, axis=(1, 2)) + b0 * b0 * hw) / m
+    assert abs(loss - (0.5 * b0 * b0 + mu * np.mean(delta ** 2))) <= 1e-14
+
+
+def test_project_mass_closed_form():
+    """An output that is the input times a complex factor c_b per state is
+    brought back to the input's mass: the result is psi_in c_b / |c_b|; a
+    state whose output mass is zero is left as it is; projecting twice
+    changes nothing."""
+    psi = W.random_field((3, 6, 7), 21)
+    c = np.array([2.0 - 1.5j, 0.25j, 0.0])
+    out = psi * c[:, None, None]
+    got = S.project_mass(psi, out)
+    for b in range(2):
+        assert np.allclose(got[b], psi[b] * c[b] / abs(c[b]), rtol=1e-14, atol=1e-15)
+        assert abs(np.sum(np.abs(got[b]) ** 2) / np.sum(np.abs(psi[b]) ** 2) - 1) < 1e-14
+    assert np.array_equal(got[2], out[2])
+    assert np.allclose(S.project_mass(psi, got), got, rtol=1e-14, atol=1e-15)
 
 
 def test_output_bias_only_network_adds_the_bias():
