@@ -13,11 +13,17 @@
  * Conventions shared by every call
  *   Layout     C order, last index fastest: a 3D grid is (N[0], N[1], N[2]) =
  *              (Nz, Ny, Nx).  Boundary sites are those with any index 0 or
- *              N[k]-1; the rest are interior.  Every N[k] >= 3.
+ *              N[k]-1; the rest are interior (a periodic grid has no
+ *              boundary sites).  Every N[k] >= 3.
  *   Psi        interleaved complex: NLSE_C128 -> double2 (re, im),
  *              NLSE_C64 -> float2, NLSE_C64_ACC64 -> double2 (the FP64 master).
  *   V          real, same shape: double for NLSE_C128, float for the other two;
- *              NULL means V = 0.
+ *              NULL means V = 0.  The library reads V when a context is
+ *              created and when nlse_refresh_potential is called: every dtype
+ *              takes max|V| for the stability check from those reads, and
+ *              NLSE_C128 integrates with a scaled copy of V made there (the
+ *              FP32 forms read V itself).  After writing new values into V,
+ *              call nlse_refresh_potential before the next nlse_step.
  *   Pointers   psi, V and workspace are DEVICE pointers owned by the caller.
  *              The library never allocates, frees or copies them; a context
  *              borrows them until nlse_destroy.  Host pointers are named *_host.
@@ -54,6 +60,11 @@ extern "C" {
 #define NLSE_BC_MSD       1 /* Eq. BCMSDdef: |Psi_b|^2 held; Eq. msd and Eq. BCMSDlap */
 #define NLSE_BC_L0        2 /* Laplacian-zero: dPsi_b/dt = i(s|Psi_b|^2 - V_b) Psi_b (Eq. BCL0dt),
                                Laplacian form D_b = 0 (Eq. BCL0lap) */
+#define NLSE_BC_PERIODIC  3 /* periodic grid, the boundary the RK4 stability analysis of Sec. 3.4
+                               assumes (not one of the paper's wall forms): no boundary sites, site
+                               N[k] along axis k is site 0 again (period N[k] h), every site is
+                               updated; mass and energy sum over every site.  Not available in the
+                               batched form. */
 
 /* ---- precision forms ---- */
 #define NLSE_C128      0 /* FP64 throughout */
@@ -86,6 +97,14 @@ size_t nlse_workspace_bytes(int dims, const int64_t *N, int dtype);
  */
 int nlse_create(nlse_t *out, int dims, const int64_t *N, double h, double a, double s, const void *V, int bc,
                 int order, int dtype, void *psi, void *workspace, size_t ws_bytes, void *stream);
+
+/*
+ * Re-read the context's potential V after the caller wrote new values into
+ * it: max|V| for the stability check and, for NLSE_C128, the scaled copy the
+ * exact-sum stages integrate with.  Synchronises the stream once (when V is
+ * not NULL).  NLSE_ECUDA on a CUDA failure.
+ */
+int nlse_refresh_potential(nlse_t ctx);
 
 /*
  * Advance Psi by nsteps RK4 steps of size dt (Eq. RK4, computed as the four
@@ -151,10 +170,32 @@ const char *nlse_last_error(void);
  * Variants 0 and 1 give bit-for-bit the same result, and so do 2 and 3.
  * Default: 2 for NLSE_C128 and 1 otherwise, except 3D grids of at most 2^18
  * sites (NLSE_C128) or 2^21 sites (the FP32 forms), which take 3 and 0.
+ * The exact-sum stencil's fixed-point scale follows the state: before every
+ * step it is taken from the largest component of Psi (so that every
+ * component has 8x headroom below the 64-bit range), at the start of each
+ * nlse_step from a pass over Psi (the caller may have written it) and after
+ * each step from the values the step wrote; a site whose operand is still
+ * out of range (a state that grew more than 8x within one step) takes the
+ * FP64 stencil.  The resolution is thus 2^-50 or finer relative to max|Psi|
+ * for any state, and results never depend on how steps are split into calls.
+ *   4 = NLSE_C64 on 3D grids: two RK4 stages per pass (stages 1+2 and 3+4,
+ *       temporal blocking): the first stage's result for a tile plus a
+ *       two-cell halo stays on chip and feeds the second stage, so the
+ *       intermediate state never goes through HBM (about 64 instead of 152
+ *       bytes per interior site and step); it applies to the 16-step chunks
+ *       nlse_step replays as CUDA graphs on grids with every extent >= 16,
+ *       an even Nx and a wall boundary, and Psi alternates with a copy in the
+ *       workspace inside each chunk (the chunk ends in Psi).  Other steps,
+ *       dtypes and grids run as 1.  Same results as 1, bit for bit.
  * tile_cfg picks the tiled kernel's CTA tile (x-by-y threads): 0 = 32x8,
  * 1 = 64x4, 2 = 32x16, 3 = 64x8, -1 = default; it never changes results.
  * Call between nlse_step calls, not during one. */
 int nlse_set_kernel(nlse_t ctx, int variant, int tile_cfg);
+
+/* The stage kernel variant nlse_step's graph-replayed steps run with, after
+ * the context's grid, dtype and boundary are taken into account (0..4 as in
+ * nlse_set_kernel), or a negative status. */
+int nlse_kernel_in_use(nlse_t ctx);
 
 /*
  * Autotuner: time every tile shape of the context's tiled kernel on its own
@@ -225,11 +266,15 @@ int nlse_batch_destroy(nlse_batch_t b);
  *   z_l = conv3x3_{dil_l}(h_{l-1}) + b_l,  h_l = silu(z_l)
  *   (l = 0 .. layers-2, `channels` channels);  y = conv3x3(h_{layers-2}) + b (2 channels);
  *   psi_out = psi_in + (y_0 + i y_1);  zero padding at the grid edges.
+ * Loss: the mean squared error of psi_out's real and imaginary parts, plus
+ * mass_weight (nlse_sur_set_mass_weight; 0 by default) times the mean over
+ * the batch's states of ((M(psi_out) - M(target)) / M(target))^2 with
+ * M = sum |psi|^2 over the state: the NLSE conserves mass, and the term
+ * teaches the network to conserve it without the projection below.
  * Activations are channels-last; every convolution (forward, backward-data,
  * weight-gradient) is an implicit GEMM on the tensor cores with BF16 operands
  * and FP32 accumulation; parameters are FP32 masters (layout per layer: W
- * [cout][9][cin] then b [cout]) with BF16 copies; loss = mean squared error of
- * psi_out's real and imaginary parts; optimiser Adam (0.9, 0.999, 1e-8).
+ * [cout][9][cin] then b [cout]) with BF16 copies; optimiser Adam (0.9, 0.999, 1e-8).
  * All pointers are device pointers owned by the caller; states are float2
  * arrays [nb][H][W].  Asynchronous unless a host output is requested.
  * ------------------------------------------------------------------------- */
@@ -252,11 +297,25 @@ int nlse_sur_init(nlse_sur_t s, uint64_t seed);
 int nlse_sur_sync_params(nlse_sur_t s);
 
 /* psi_out = network(psi_in) for nb states (nb <= max_batch).  With
+ * masses_out (device, 2 nb doubles; NULL to skip) state b's sums
+ * M(psi_in) = sum |psi_in|^2 and M(raw) = sum |psi_out|^2 of the network's
+ * output as it came out, before any projection, go to masses_out[2b] and
+ * masses_out[2b + 1] (FP64, fixed summation order): the raw output's mass is
+ * what a caller judges the network's mass conservation by.  With
  * project_mass != 0 each output state is then rescaled by
- * sqrt(M(psi_in) / M(psi_out)) (sums of |psi|^2 in FP64), so that it carries
- * its input's mass, which the NLSE conserves; a state whose output mass is 0
- * is left as it is.  psi_out must not overlap psi_in. */
-int nlse_sur_forward(nlse_sur_t s, int nb, const void *psi_in, void *psi_out, int project_mass);
+ * sqrt(M(psi_in) / M(raw)), so that it carries its input's mass, which the
+ * NLSE conserves; a state whose output mass is 0 is left as it is.  psi_out
+ * must not overlap psi_in. */
+int nlse_sur_forward(nlse_sur_t s, int nb, const void *psi_in, void *psi_out, int project_mass, double *masses_out);
+
+/* Weight of the mass term of the training loss (see above), >= 0. */
+int nlse_sur_set_mass_weight(nlse_sur_t s, double mass_weight);
+
+/* Relative L2 distance ||a_b - b_b|| / ||b_b|| of nb state pairs (device
+ * float2 [nb][H][W] each) in FP64 with a fixed summation order, into the
+ * host array rel_l2_host[nb]; synchronises the stream.  (The rollout's check
+ * of a predicted window against the RK4 window.) */
+int nlse_sur_compare(nlse_sur_t s, int nb, const void *a, const void *b, double *rel_l2_host);
 
 /* Loss gradient w.r.t. every parameter for (psi_in, psi_target) into grad_out
  * (device, param layout; NULL to skip) and the loss into *loss_out (host;
@@ -319,7 +378,7 @@ int nlse_mass_noalloc(int dims, const int64_t *N, double h, int dtype, const voi
                       void *stream);
 
 /*
- * Test hooks for the bounded device-side waits (not needed in normal use).
+ * Test hooks (not needed in normal use).
  *   NLSE_DEBUG_SPIN_LIMIT  value = SM clock cycles any device-side wait may
  *                          last before the kernel gives up (default ~2e9,
  *                          about a second).
@@ -328,12 +387,18 @@ int nlse_mass_noalloc(int dims, const int64_t *N, double h, int dtype, const voi
  *                          beyond what its copy delivers, so its wait runs out
  *                          without any fault; the next nlse_sync then returns
  *                          NLSE_ETIMEOUT once.  0 restores normal operation.
+ *   NLSE_DEBUG_FIX_OFFSET  value (-64..64) added to the exact-sum stencil's
+ *                          fraction bits after they are derived from Psi:
+ *                          positive values shrink its range below the state,
+ *                          so that the FP64 out-of-range fallback runs at
+ *                          every site; 0 restores normal operation.
  * Psi is not valid after a step that timed out; reporting NLSE_ETIMEOUT
  * clears every status flag (including a non-finite flag the invalid step
  * may have raised), and the context stays usable once Psi is restored.
  */
 #define NLSE_DEBUG_SPIN_LIMIT 1
 #define NLSE_DEBUG_EXTRA_TX   2
+#define NLSE_DEBUG_FIX_OFFSET 3
 int nlse_debug_set(nlse_t ctx, int key, long long value);
 
 #ifdef __cplusplus

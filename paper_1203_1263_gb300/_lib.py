@@ -29,6 +29,7 @@ C64 = 1
 C64_ACC64 = 2
 DEBUG_SPIN_LIMIT = 1
 DEBUG_EXTRA_TX = 2
+DEBUG_FIX_OFFSET = 3
 
 STATUS_NAMES = {0: "NLSE_OK", -1: "NLSE_EINVAL", -2: "NLSE_ENOMEM", -3: "NLSE_ECUDA", -4: "NLSE_EUNSTABLE",
                 -5: "NLSE_ENONFINITE", -6: "NLSE_ETIMEOUT", -7: "NLSE_ESTATE"}
@@ -43,6 +44,7 @@ SIGNATURES = {
     "nlse_create": (_I, [ctypes.POINTER(_VP), _I, _I64P, _D, _D, _D, _VP, _I, _I, _I, _VP, _VP, ctypes.c_size_t,
                          _VP]),
     "nlse_step": (_I, [_VP, ctypes.c_int64, _D]),
+    "nlse_refresh_potential": (_I, [_VP]),
     "nlse_mass": (_I, [_VP, ctypes.POINTER(_D)]),
     "nlse_energy": (_I, [_VP, ctypes.POINTER(_D)]),
     "nlse_rhs": (_I, [_VP, _VP, _VP]),
@@ -51,6 +53,7 @@ SIGNATURES = {
     "nlse_destroy": (_I, [_VP]),
     "nlse_last_error": (ctypes.c_char_p, []),
     "nlse_set_kernel": (_I, [_VP, _I, _I]),
+    "nlse_kernel_in_use": (_I, [_VP]),
     "nlse_debug_set": (_I, [_VP, _I, ctypes.c_longlong]),
     "nlse_autotune": (_I, [_VP, ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_float)]),
     "nlse_mass_noalloc": (_I, [_I, _I64P, _D, _I, _VP, _VP, _VP]),
@@ -67,7 +70,9 @@ SIGNATURES = {
                              _VP]),
     "nlse_sur_init": (_I, [_VP, ctypes.c_uint64]),
     "nlse_sur_sync_params": (_I, [_VP]),
-    "nlse_sur_forward": (_I, [_VP, _I, _VP, _VP, _I]),
+    "nlse_sur_forward": (_I, [_VP, _I, _VP, _VP, _I, _VP]),
+    "nlse_sur_set_mass_weight": (_I, [_VP, _D]),
+    "nlse_sur_compare": (_I, [_VP, _I, _VP, _VP, ctypes.POINTER(_D)]),
     "nlse_sur_gradients": (_I, [_VP, _I, _VP, _VP, _VP, ctypes.POINTER(_D)]),
     "nlse_sur_train_step": (_I, [_VP, _I, _VP, _VP, ctypes.c_float, ctypes.c_float, ctypes.POINTER(_D)]),
     "nlse_sur_set_kernel": (_I, [_VP, _I]),

@@ -61,7 +61,7 @@ constexpr size_t kAlign = 256;
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 struct Layout {
-  size_t ktot, ptmp, pout, pn32, vs, partials, status, total;
+  size_t ktot, ptmp, pout, pn32, vs, alt, partials, status, total;
 };
 
 bool layout_for(int dims, const int64_t* N, int dtype, Layout* L, int64_t* total_sites) {
@@ -80,6 +80,7 @@ bool layout_for(int dims, const int64_t* N, int dtype, Layout* L, int64_t* total
   L->pout = off; off = align_up(off + es * total);
   L->pn32 = off; if (dtype == NLSE_C64_ACC64) off = align_up(off + 8 * total);
   L->vs = off; if (dtype == NLSE_C128) off = align_up(off + 8 * total);   // V / cLF for the exact-sum stages
+  L->alt = off; if (dtype == NLSE_C64 && dims == 3) off = align_up(off + 8 * total);   // Psi ping-pong (fused step)
   L->partials = off; off = align_up(off + sizeof(double) * 2 * kMaxReduceBlocks);
   L->status = off; off = align_up(off + 256);
   L->total = off;
@@ -101,7 +102,8 @@ struct nlse_ctx {
   char* ws;
   Layout lay;
   double vmax;
-  int fixF;          // fraction bits of the exact-sum stencil (FP64 path)
+  int fixF;          // reference fraction bits F0 of the exact-sum stencil (FP64 path): cLF = cL 2^-F0
+  int fix_offset;    // test hook added to the derived fraction bits (nlse_debug_set)
   int variant, tile_cfg;
   cudaStream_t cap;
   cudaGraphExec_t exec;
@@ -110,6 +112,8 @@ struct nlse_ctx {
   // TMA descriptors of the stage inputs (Psi or its FP32 copy, Psi_tmp, Psi_out) per tile shape
   CUtensorMap tmaps[4][3];
   signed char tmap_state[4][3];   // 0 = not built, 1 = ok, -1 = layout not eligible
+  CUtensorMap fmaps[3];           // the fused kernel's inputs: Psi, its ping-pong copy, Psi_out
+  signed char fmap_state[3];
   long long spin_limit;           // bound on device-side waits (cycles)
   unsigned int extra_tx;          // test hook, see nlse_debug_set
   cudaStream_t side;              // wall-shell kernels run here, concurrently with the deep kernels
@@ -118,6 +122,9 @@ struct nlse_ctx {
   void* at(size_t off) const { return ws + off; }
   unsigned int* flag() const { return (unsigned int*)(ws + lay.status); }
   unsigned long long* vbits() const { return (unsigned long long*)(ws + lay.status + 8); }
+  int* fdev() const { return (int*)(ws + lay.status + 16); }                    // current fraction bits
+  unsigned int* emax() const { return (unsigned int*)(ws + lay.status + 20); }  // stage-4 largest exponent
+  bool exact() const { return dtype == NLSE_C128 && variant >= 2 && variant <= 3; }
   double* result() const { return (double*)(ws + lay.status + 64); }
   double* partials() const { return (double*)(ws + lay.partials); }
 };
@@ -157,6 +164,7 @@ Field<T> make_field(const nlse_ctx* c, const void* in) {
   f.tiny = R(sizeof(R) == 8 ? 1e-300 : 1e-30);
   f.bc = c->bc;
   f.F = c->fixF;
+  f.Fdev = (c->dtype == NLSE_C128) ? c->fdev() : nullptr;
   f.cLF = ldexp(c->order == 4 ? c->a / (12.0 * c->h * c->h) : c->a / (c->h * c->h), -c->fixF);
   f.invcLF = R(1.0 / f.cLF);
   f.sG = R(c->s / f.cLF);
@@ -165,17 +173,13 @@ Field<T> make_field(const nlse_ctx* c, const void* in) {
   return f;
 }
 
+LaunchCfg launch_cfg(const nlse_ctx* c);
+
 template <class T>
 cudaError_t dispatch_stage(const nlse_ctx* c, const StageArgs<T>& A, const void* tmap, cudaStream_t st) {
-  LaunchCfg L;
-  L.variant = c->variant;
-  L.tile_cfg = resolved_tile(c);
+  LaunchCfg L = launch_cfg(c);
+  L.variant = (c->variant == 4) ? 1 : c->variant;   // single stages of the fused variant: the tiled kernel
   L.tmap = tmap;
-  L.spin_limit = c->spin_limit;
-  L.extra_tx = c->extra_tx;
-  L.side = c->side;
-  L.ev_fork = c->ev_fork;
-  L.ev_join = c->ev_join;
   switch (c->d * 10 + c->order) {
     case 12: return launch_stage<T, 1, 2>(A, L, st);
     case 14: return launch_stage<T, 1, 4>(A, L, st);
@@ -186,12 +190,45 @@ cudaError_t dispatch_stage(const nlse_ctx* c, const StageArgs<T>& A, const void*
   }
 }
 
+// A 3D TMA descriptor over a complex field of the context's shape (real components of es bytes) with a
+// box of box_x components by box_y rows by one plane; false when the layout is not eligible (TMA needs
+// 16-byte row pitches and a 16-byte aligned base).
+bool encode_field_map(const nlse_ctx* c, CUtensorMap* m, const void* ptr, size_t es, int box_x, int box_y) {
+  const cuuint64_t nx = c->n[2], ny = c->n[1], nz = c->n[0];
+  EncodeTiledFn fn = encode_fn();
+  if (!fn || (2 * nx * es) % 16 != 0 || ((uintptr_t)ptr % 16) != 0) return false;
+  cuuint64_t dims[3] = {2 * nx, ny, nz};
+  cuuint64_t strides[2] = {2 * nx * es, 2 * nx * ny * es};
+  cuuint32_t box[3] = {cuuint32_t(box_x), cuuint32_t(box_y), 1};
+  cuuint32_t estr[3] = {1, 1, 1};
+  return fn(m, es == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void*>(ptr),
+            dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// The fused kernel's TMA descriptor of buffer `buf` (0 = Psi, 1 = its ping-pong copy, 2 = Psi_out).
+const CUtensorMap* fused_tmap(const nlse_ctx* cc, int buf, const void* ptr) {
+  nlse_ctx* c = const_cast<nlse_ctx*>(cc);
+  signed char& st = c->fmap_state[buf];
+  if (st == 0) st = encode_field_map(c, &c->fmaps[buf], ptr, 4, kFusedBoxX, kFusedBoxY) ? 1 : -1;
+  return st == 1 ? &c->fmaps[buf] : nullptr;
+}
+
+// The fused step runs for the FP32 form on 3D grids with every extent >= 16
+// and TMA-eligible rows, except on periodic grids (their shell wraps).
+bool fused_path(const nlse_ctx* c) {
+  if (c->variant != 4 || c->dtype != NLSE_C64 || c->d != 3 || c->bc == NLSE_BC_PERIODIC) return false;
+  const int n[3] = {int(c->n[0]), int(c->n[1]), int(c->n[2])};
+  if (!fused_grid_ok(3, n)) return false;
+  return fused_tmap(c, 0, c->psi) && fused_tmap(c, 1, c->at(c->lay.alt)) && fused_tmap(c, 2, c->at(c->lay.pout));
+}
+
 // The TMA descriptor of stage-input buffer `buf` (0 = Psi or its FP32 copy,
 // 1 = Psi_tmp, 2 = Psi_out) for the 3D tiled kernel's tile, or nullptr when
 // the layout is not eligible (TMA needs 16-byte row pitches).
 const CUtensorMap* stage_tmap(const nlse_ctx* cc, int buf, const void* ptr) {
   nlse_ctx* c = const_cast<nlse_ctx*>(cc);
-  if (c->d != 3 || (c->variant != 1 && c->variant != 2)) return nullptr;
+  if (c->d != 3 || (c->variant != 1 && c->variant != 2 && c->variant != 4)) return nullptr;
   const int tc = resolved_tile(c);
   signed char& st = c->tmap_state[tc][buf];
   if (st == 0) {
@@ -215,18 +252,19 @@ const CUtensorMap* stage_tmap(const nlse_ctx* cc, int buf, const void* ptr) {
   return st == 1 ? &c->tmaps[tc][buf] : nullptr;
 }
 
-// Stage s (1..4) of Eq. RK4_GPU: Psi -> Psi_tmp -> Psi_out -> Psi_tmp -> Psi.
+// The arguments of stage s (1..4) of Eq. RK4_GPU: Psi -> Psi_tmp -> Psi_out ->
+// Psi_tmp -> Psi.  cur holds Psi^n, stage 4 writes Psi^{n+1} to nxt (the same
+// buffer except on the fused path's ping-pong steps).
 template <class T>
-cudaError_t launch_one_stage(const nlse_ctx* c, int s, double dt, cudaStream_t st) {
+StageArgs<T> stage_args(const nlse_ctx* c, int s, double dt, void* cur, void* nxt) {
   using C = typename T::C;
   using R = typename T::R;
   const bool mix = (c->dtype == NLSE_C64_ACC64);
   C* ktot = (C*)c->at(c->lay.ktot);
   C* ptmp = (C*)c->at(c->lay.ptmp);
   C* pout = (C*)c->at(c->lay.pout);
-  const C* psin = mix ? (const C*)c->at(c->lay.pn32) : (const C*)c->psi;
+  const C* psin = mix ? (const C*)c->at(c->lay.pn32) : (const C*)cur;
   const void* in[4] = {psin, ptmp, pout, ptmp};
-  const int inbuf[4] = {0, 1, 2, 1};
   C* outs[4] = {ptmp, pout, ptmp, nullptr};
   const double dtc[4] = {dt / 2.0, dt / 2.0, dt, dt / 6.0};
   const int i = s - 1;
@@ -236,16 +274,55 @@ cudaError_t launch_one_stage(const nlse_ctx* c, int s, double dt, cudaStream_t s
   A.psin = psin;
   A.ktot = ktot;
   A.out = outs[i];
-  A.master = (typename T::M*)c->psi;
+  A.master = (typename T::M*)nxt;
+  A.master_in = (const typename T::M*)cur;
   A.n32 = mix ? (C*)c->at(c->lay.pn32) : nullptr;
   // FP64 with the exact-sum stencil: F is formed in units of cLF, so the stage coefficient carries it
-  const bool g = std::is_same<T, P64>::value && c->variant >= 2;
+  const bool g = std::is_same<T, P64>::value && c->exact();
   A.dtc = R(g ? dtc[i] * A.f.cLF : dtc[i]);
   A.dt6 = dt / 6.0;
   A.stage = s;
   A.flag = c->flag();
   A.Vs = (g && c->V) ? (const typename T::VR*)c->at(c->lay.vs) : nullptr;
-  return dispatch_stage<T>(c, A, stage_tmap(c, inbuf[i], in[i]), st);
+  A.emax = (g && s == 4) ? c->emax() : nullptr;   // collects the exponent of Psi^{n+1}
+  return A;
+}
+
+// Stage s of one step, Psi updated in place.
+template <class T>
+cudaError_t launch_one_stage(const nlse_ctx* c, int s, double dt, cudaStream_t st) {
+  const StageArgs<T> A = stage_args<T>(c, s, dt, c->psi, c->psi);
+  const int inbuf[4] = {0, 1, 2, 1};
+  return dispatch_stage<T>(c, A, stage_tmap(c, inbuf[s - 1], A.f.in), st);
+}
+
+LaunchCfg launch_cfg(const nlse_ctx* c) {
+  LaunchCfg L;
+  L.variant = c->variant;
+  L.tile_cfg = resolved_tile(c);
+  L.tmap = nullptr;
+  L.spin_limit = c->spin_limit;
+  L.extra_tx = c->extra_tx;
+  L.side = c->side;
+  L.ev_fork = c->ev_fork;
+  L.ev_join = c->ev_join;
+  return L;
+}
+
+// One step of the fused path from buffer cur to buffer nxt (Psi or its ping-pong copy).
+cudaError_t launch_step_fused(const nlse_ctx* c, double dt, cudaStream_t st, void* cur, void* nxt) {
+  StageArgs<P32> A[4];
+  for (int s = 1; s <= 4; ++s) A[s - 1] = stage_args<P32>(c, s, dt, cur, nxt);
+  const CUtensorMap* tm12 = fused_tmap(c, cur == c->psi ? 0 : 1, cur);
+  const CUtensorMap* tm34 = fused_tmap(c, 2, c->at(c->lay.pout));
+  const LaunchCfg L = launch_cfg(c);
+  return c->order == 4 ? launch_fused_step<4>(A, tm12, tm34, L, st) : launch_fused_step<2>(A, tm12, tm34, L, st);
+}
+
+// The exact-sum stencil's scale for the next step: from the exponent stage 4
+// collected (psi == nullptr) or from a full pass over psi.
+cudaError_t update_fix(const nlse_ctx* c, const void* psi, cudaStream_t st) {
+  return launch_fix_update((const double*)psi, 2 * c->total, c->emax(), c->fdev(), c->fixF, c->fix_offset, st);
 }
 
 template <class T>
@@ -254,6 +331,7 @@ cudaError_t launch_step(const nlse_ctx* c, double dt, cudaStream_t st) {
     cudaError_t e = launch_one_stage<T>(c, s, dt, st);
     if (e != cudaSuccess) return e;
   }
+  if (std::is_same<T, P64>::value && c->exact()) return update_fix(c, nullptr, st);
   return cudaSuccess;
 }
 
@@ -288,7 +366,16 @@ int ensure_graph(nlse_ctx* c, double dt) {
   cudaError_t e = cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) return cuda_fail(e, "cudaStreamBeginCapture");
   cudaError_t le = cudaSuccess;
-  for (int i = 0; i < kGraphSteps && le == cudaSuccess; ++i) le = launch_step_any(c, dt, c->cap);
+  const bool fused = fused_path(c);
+  for (int i = 0; i < kGraphSteps && le == cudaSuccess; ++i) {
+    if (fused) {   // ping-pong: even steps Psi -> copy, odd steps copy -> Psi (kGraphSteps is even)
+      void* a = c->psi;
+      void* b = c->at(c->lay.alt);
+      le = (i % 2 == 0) ? launch_step_fused(c, dt, c->cap, a, b) : launch_step_fused(c, dt, c->cap, b, a);
+    } else {
+      le = launch_step_any(c, dt, c->cap);
+    }
+  }
   cudaGraph_t g = nullptr;
   e = cudaStreamEndCapture(c->cap, &g);
   if (le != cudaSuccess) { if (g) cudaGraphDestroy(g); return cuda_fail(le, "stage launch (capture)"); }
@@ -384,8 +471,8 @@ int nlse_create(nlse_t* out, int dims, const int64_t* N, double h, double a, dou
   if (!(h > 0) || !isfinite(h)) return fail(NLSE_EINVAL, "h must be > 0");
   if (!(a > 0) || !isfinite(a)) return fail(NLSE_EINVAL, "a must be > 0");
   if (!isfinite(s)) return fail(NLSE_EINVAL, "s must be finite");
-  if (bc != NLSE_BC_DIRICHLET && bc != NLSE_BC_MSD && bc != NLSE_BC_L0)
-    return fail(NLSE_EINVAL, "bc must be 0, 1 or 2");
+  if (bc != NLSE_BC_DIRICHLET && bc != NLSE_BC_MSD && bc != NLSE_BC_L0 && bc != NLSE_BC_PERIODIC)
+    return fail(NLSE_EINVAL, "bc must be 0, 1, 2 or 3");
   if (order != 2 && order != 4) return fail(NLSE_EINVAL, "order must be 2 or 4");
   if (!psi) return fail(NLSE_EINVAL, "psi is NULL");
   if (!workspace) return fail(NLSE_EINVAL, "workspace is NULL");
@@ -447,6 +534,7 @@ int nlse_create(nlse_t* out, int dims, const int64_t* N, double h, double a, dou
     const Field<P64> f = make_field<P64>(c, psi);
     e = launch_scale_v((const double*)V, 1.0 / f.cLF, total, (double*)c->at(L.vs), c->stream);
   }
+  if (e == cudaSuccess && dtype == NLSE_C128) e = update_fix(c, psi, c->stream);
   if (e != cudaSuccess) {
     nlse_destroy(c);
     return cuda_fail(e, "nlse_create");
@@ -457,11 +545,40 @@ int nlse_create(nlse_t* out, int dims, const int64_t* N, double h, double a, dou
 
 int nlse_set_kernel(nlse_t c, int variant, int tile_cfg) {
   if (!c) return fail(NLSE_EINVAL, "NULL context");
-  if (variant < 0 || variant > 3) return fail(NLSE_EINVAL, "variant must be 0..3");
+  if (variant < 0 || variant > 4) return fail(NLSE_EINVAL, "variant must be 0..4");
   if (tile_cfg < -1 || tile_cfg > 3) return fail(NLSE_EINVAL, "tile_cfg must be -1..3");
   c->variant = variant;
   c->tile_cfg = tile_cfg;
   drop_graph(c);
+  return NLSE_OK;
+}
+
+int nlse_kernel_in_use(nlse_t c) {
+  if (!c) return fail(NLSE_EINVAL, "NULL context");
+  if (fused_path(c)) return 4;
+  if (c->variant == 4) return c->d == 1 ? 0 : 1;
+  if (c->d == 1) return (c->dtype == NLSE_C128 && c->variant >= 2) ? 3 : 0;
+  if (c->dtype != NLSE_C128 && c->variant >= 2) return c->variant - 2;
+  return c->variant;
+}
+
+int nlse_refresh_potential(nlse_t c) {
+  if (!c) return fail(NLSE_EINVAL, "NULL context");
+  cudaError_t e = cudaSuccess;
+  double vmax = 0.0;
+  if (c->V) {
+    e = launch_vmax(c->V, c->dtype == NLSE_C128, c->total, c->vbits(), c->stream);
+    unsigned long long bits = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&bits, c->vbits(), sizeof(bits), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    memcpy(&vmax, &bits, sizeof(double));
+    if (e == cudaSuccess && c->dtype == NLSE_C128) {
+      const Field<P64> f = make_field<P64>(c, c->psi);
+      e = launch_scale_v((const double*)c->V, 1.0 / f.cLF, c->total, (double*)c->at(c->lay.vs), c->stream);
+    }
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "nlse_refresh_potential");
+  c->vmax = vmax;
   return NLSE_OK;
 }
 
@@ -476,6 +593,8 @@ int nlse_step(nlse_t c, int64_t nsteps, double dt) {
   if (c->dtype == NLSE_C64_ACC64)
     e = launch_round_master((const double2*)c->psi, (float2*)c->at(c->lay.pn32), c->total, c->stream);
   if (e != cudaSuccess) return cuda_fail(e, "round master");
+  // the exact-sum scale of the state as the caller left it (stage 4 keeps it current from here on)
+  if (c->exact() && (e = update_fix(c, c->psi, c->stream)) != cudaSuccess) return cuda_fail(e, "scale");
   int64_t left = nsteps;
   if (nsteps >= kGraphSteps) {
     int rc = ensure_graph(c, dt);
@@ -495,6 +614,7 @@ int nlse_step(nlse_t c, int64_t nsteps, double dt) {
 int nlse_rhs(nlse_t c, const void* psi_in, void* F_out) {
   if (!c || !psi_in || !F_out) return fail(NLSE_EINVAL, "NULL argument");
   cudaError_t e;
+  if (c->exact() && (e = update_fix(c, psi_in, c->stream)) != cudaSuccess) return cuda_fail(e, "scale");
   auto run = [&](auto tag) {
     using T = decltype(tag);
     StageArgs<T> A;
@@ -624,6 +744,7 @@ int nlse_autotune(nlse_t c, int* best_tile_cfg, float* best_ms) {
     cudaError_t e = cudaSuccess;
     if (c->dtype == NLSE_C64_ACC64)
       e = launch_round_master((const double2*)c->psi, (float2*)c->at(c->lay.pn32), c->total, c->stream);
+    if (e == cudaSuccess && c->exact()) e = update_fix(c, c->psi, c->stream);
     for (int t = 0; t < 4 && e == cudaSuccess; ++t) {
       c->tile_cfg = t;
       e = launch_stage_any(c, 1, 1e-12, c->stream);
@@ -661,6 +782,10 @@ int nlse_debug_set(nlse_t c, int key, long long value) {
     case NLSE_DEBUG_EXTRA_TX:
       if (value < 0 || value > (1 << 20) || value % 16) return fail(NLSE_EINVAL, "extra_tx must be 0..2^20, multiple of 16");
       c->extra_tx = (unsigned int)value;
+      break;
+    case NLSE_DEBUG_FIX_OFFSET:
+      if (value < -64 || value > 64) return fail(NLSE_EINVAL, "fix offset must be -64..64");
+      c->fix_offset = (int)value;
       break;
     default:
       return fail(NLSE_EINVAL, "unknown debug key");

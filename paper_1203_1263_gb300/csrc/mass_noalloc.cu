@@ -148,16 +148,18 @@ int nlse_mass_noalloc(int dims, const int64_t* N, double h, int dtype, const voi
   if (dtype != NLSE_C128 && dtype != NLSE_C64 && dtype != NLSE_C64_ACC64) return fail(NLSE_EINVAL, "bad dtype");
   if (!(h > 0) || !isfinite(h)) return fail(NLSE_EINVAL, "h must be > 0");
   if (!psi || !out) return fail(NLSE_EINVAL, "psi and out must be device pointers");
+  // the site count, checked against the limit before each multiplication (no int64 overflow)
+  const int64_t limit = (int64_t)kMaxBlocks * kSitesPerBlock;
   int64_t total = 1;
-  for (int k = 0; k < dims; ++k) {
+  for (int k = 0; k < dims; ++k)
     if (N[k] < 1) return fail(NLSE_EINVAL, "every N must be >= 1");
+  for (int k = 0; k < dims; ++k) {
+    if (N[k] > limit / total)
+      return fail(NLSE_EINVAL, "grid exceeds the no-alloc maximum of %lld sites (%d blocks of %d sites)",
+                  (long long)limit, kMaxBlocks, kSitesPerBlock);
     total *= N[k];
-    if (total > (int64_t)kMaxBlocks * kSitesPerBlock) break;
   }
   const int64_t nb = (total + kSitesPerBlock - 1) / kSitesPerBlock;
-  if (nb > kMaxBlocks)
-    return fail(NLSE_EINVAL, "grid of %lld sites exceeds the no-alloc maximum of %lld sites (%d blocks of %d)",
-                (long long)total, (long long)kMaxBlocks * kSitesPerBlock, kMaxBlocks, kSitesPerBlock);
   double* scratch = nullptr;
   int rc = scratch_for_current_device(&scratch);
   if (rc != NLSE_OK) return rc;

@@ -32,7 +32,7 @@
 
 namespace nlse {
 
-enum { BC_DIRICHLET = 0, BC_MSD = 1, BC_L0 = 2 };
+enum { BC_DIRICHLET = 0, BC_MSD = 1, BC_L0 = 2, BC_PERIODIC = 3 };
 
 template <class R> struct V2;
 template <> struct V2<double> { using t = double2; };
@@ -74,7 +74,9 @@ struct Field {
   R cL;              // a / (12 h^2) for order 4, a / h^2 for order 2
   R tiny;            // MSD guard on |Psi_{b-1}|^2
   int bc;
-  int F;             // exact-sum stencil: fixed-point fraction bits
+  int F;             // exact-sum stencil: the reference fraction bits F0 that cLF and V / cLF are scaled by
+  const int* Fdev;   // exact-sum stencil: device word holding the fraction bits of the current state
+                     //   (derived from max |Psi| every step; nullptr: use F)
   double cLF;        // exact-sum stencil: cL * 2^-F
   R sG;              // exact-sum stencil: s / cLF
   R invcLF;          // exact-sum stencil: 1 / cLF
@@ -151,15 +153,17 @@ __device__ __forceinline__ typename V2<typename T::R>::t a_lap_body(const Field<
                                                                     typename T::R Nc) {
   using R = typename T::R;
   using C2 = typename V2<R>::t;
+  // Sums of differences from the centre: Psi_{+-k} - Psi_c is exact for nearby values (Sterbenz), so the
+  // large cancellation of the stencil (centre weight 30 d in 2SHOC) happens before any rounding.
   C2 s1 = {R(0), R(0)};
 #pragma unroll
   for (int k = 0; k < D; ++k) {
     const C2 u = acc.at1(k, 1);
     const C2 w = acc.at1(k, -1);
-    s1.x += u.x + w.x;
-    s1.y += u.y + w.y;
+    s1.x += (u.x - pc.x) + (w.x - pc.x);
+    s1.y += (u.y - pc.y) + (w.y - pc.y);
   }
-  const C2 dh = {fma(R(-2 * D), pc.x, s1.x), fma(R(-2 * D), pc.y, s1.y)};   // h^2 D_c
+  const C2 dh = s1;   // h^2 D_c
   if constexpr (ORDER == 2) {
     return {f.cL * dh.x, f.cL * dh.y};
   }
@@ -171,10 +175,11 @@ __device__ __forceinline__ typename V2<typename T::R>::t a_lap_body(const Field<
     else lo = ghost<T, D>(f, acc, k, -1, c, pc, dh, Nc);
     if (!WALL || idx[k] <= f.n[k] - 3) hi = acc.at1(k, 2);
     else hi = ghost<T, D>(f, acc, k, 1, c, pc, dh, Nc);
-    s2.x += lo.x + hi.x;
-    s2.y += lo.y + hi.y;
+    s2.x += (lo.x - pc.x) + (hi.x - pc.x);
+    s2.y += (lo.y - pc.y) + (hi.y - pc.y);
   }
-  return {f.cL * fma(R(-30 * D), pc.x, fma(R(16), s1.x, -s2.x)), f.cL * fma(R(-30 * D), pc.y, fma(R(16), s1.y, -s2.y))};
+  // 16 (s1 + 2d Psi_c) - (s2 + 2d Psi_c) - 30 d Psi_c = 16 s1 - s2
+  return {f.cL * fma(R(16), s1.x, -s2.x), f.cL * fma(R(16), s1.y, -s2.y)};
 }
 
 template <class T, int D, int ORDER, class Acc>
@@ -228,6 +233,26 @@ __device__ __forceinline__ long long fix1(double v, int F) {
   return (u >> 63) ? -r : r;
 }
 __device__ __forceinline__ longlong2 fix2(double2 v, int F) { return make_longlong2(fix1(v.x, F), fix1(v.y, F)); }
+
+// The fraction bits the exact-sum stencil uses for the current state: F is
+// re-derived on the device before every step from the largest component of
+// Psi^n (|v| < 2^(54 - F) with 8x headroom), so the fixed-point resolution
+// 2^-F always follows the state's own scale.  The stencil sums are formed at
+// that scale and converted to units of cLF = cL 2^-F0 (F0: the reference
+// scale fixed at creation) by an exact power-of-two exponent shift.
+template <class T>
+__device__ __forceinline__ int cur_fix(const Field<T>& f) { return f.Fdev ? __ldg(f.Fdev) : f.F; }
+
+// Biased IEEE-754 exponent of |v|: 0 for zero and subnormals, 2047 for Inf/NaN.
+__device__ __forceinline__ unsigned int expo_bits(double v) { return (unsigned int)(__double2hiint(v) >> 20) & 0x7FFu; }
+__device__ __forceinline__ unsigned int expo_bits(float v) { return 0u; }
+
+// Largest biased exponent over a full warp into *p (one atomic per warp, skipped when *p is already as
+// large).  Every lane of the warp must call it.
+__device__ __forceinline__ void emax_commit(unsigned int* p, unsigned int e) {
+  e = __reduce_max_sync(0xffffffffu, e);
+  if ((threadIdx.x & 31) == 0 && e > __ldcg(p)) atomicMax(p, e);
+}
 __device__ __forceinline__ bool fbad(longlong2 v) { return (v.x == kFixBad) | (v.y == kFixBad); }
 
 // The FP64 stencil as an out-of-line call (out-of-range operands).
@@ -242,7 +267,7 @@ __device__ __forceinline__ double2 a_lap_slow(const Field<T>& f, const Acc& acc,
 // the values beyond the wall.  Out of line: only wall-adjacent sites call it.
 template <class T, int D, class Acc>
 __device__ __forceinline__ longlong2 exact_s2_wall(const Field<T>& f, const Acc& acc, const int* idx, int64_t c,
-                                                double2 pc, double Nc, bool* bad) {
+                                                double2 pc, double Nc, int F, bool* bad) {
   double2 t = {0.0, 0.0};
 #pragma unroll
   for (int k = 0; k < D; ++k) {
@@ -257,9 +282,9 @@ __device__ __forceinline__ longlong2 exact_s2_wall(const Field<T>& f, const Acc&
   for (int k = 0; k < D; ++k) {
     longlong2 lo, hi;
     if (idx[k] >= 2) lo = acc.fx1(k, -2);
-    else lo = fix2(ghost<T, D>(f, acc, k, -1, c, pc, dh, Nc), f.F);
+    else lo = fix2(ghost<T, D>(f, acc, k, -1, c, pc, dh, Nc), F);
     if (idx[k] <= f.n[k] - 3) hi = acc.fx1(k, 2);
-    else hi = fix2(ghost<T, D>(f, acc, k, 1, c, pc, dh, Nc), f.F);
+    else hi = fix2(ghost<T, D>(f, acc, k, 1, c, pc, dh, Nc), F);
     b |= fbad(lo) | fbad(hi);
     sx += lo.x + hi.x;
     sy += lo.y + hi.y;
@@ -268,10 +293,12 @@ __device__ __forceinline__ longlong2 exact_s2_wall(const Field<T>& f, const Acc&
   return make_longlong2(sx, sy);
 }
 
-// int64 -> double with IEEE-754 round-to-nearest-even, on the integer pipe
-// (the hardware conversion runs on the FP64 pipe, GB300's scarcest unit).
-// Exact for |v| < 2^53; one correctly rounded result otherwise.
-__device__ __forceinline__ double i2d_rn(long long v) {
+// int64 -> double with IEEE-754 round-to-nearest-even, times 2^eadj, on the
+// integer pipe (the hardware conversion runs on the FP64 pipe, GB300's
+// scarcest unit): the power of two only moves the exponent, so the result is
+// the correctly rounded v 2^eadj.  Exact for |v| < 2^53.  A result outside
+// the normal range (never for the scales the stencil uses) takes ldexp.
+__device__ __forceinline__ double i2d_rn(long long v, int eadj = 0) {
   if (v == 0) return 0.0;
   const unsigned long long sgn = (unsigned long long)v & 0x8000000000000000ull;
   unsigned long long u = sgn ? 0ull - (unsigned long long)v : (unsigned long long)v;
@@ -286,7 +313,11 @@ __device__ __forceinline__ double i2d_rn(long long v) {
     if (rem > half || (rem == half && (m & 1ull))) ++m;
     if (m == (1ull << 53)) { m >>= 1; ++e; }
   }
-  return __longlong_as_double((long long)(sgn | ((unsigned long long)(e + 1023) << 52) | (m & 0x000FFFFFFFFFFFFFull)));
+  const int be = e + 1023 + eadj;
+  if (be >= 1 && be <= 2046)
+    return __longlong_as_double((long long)(sgn | ((unsigned long long)be << 52) | (m & 0x000FFFFFFFFFFFFFull)));
+  return ldexp(__longlong_as_double((long long)(sgn | ((unsigned long long)(e + 1023) << 52) |
+                                                (m & 0x000FFFFFFFFFFFFFull))), eadj);
 }
 
 // The exact-sum Laplacian in units of cLF = cL 2^-F (the exact integer sum
@@ -296,6 +327,7 @@ template <class T, int D, int ORDER, class Acc>
 __device__ __forceinline__ double2 a_lap_exact(const Field<T>& f, const Acc& acc, const int* idx, int64_t c,
                                                double2 pc, double Ng) {
   static_assert(std::is_same<typename T::R, double>::value, "exact-sum stencil is FP64 only");
+  const int F = cur_fix(f), eadj = f.F - F;
   const longlong2 cc = acc.fx0();
   bool bad = fbad(cc);
   long long s1x = 0, s1y = 0;
@@ -312,7 +344,7 @@ __device__ __forceinline__ double2 a_lap_exact(const Field<T>& f, const Acc& acc
       const double2 aL = a_lap_slow<T, D, ORDER>(f, acc, idx, c, pc, Nc);
       return {aL.x * f.invcLF, aL.y * f.invcLF};
     }
-    return {i2d_rn(s1x - 2 * D * cc.x), i2d_rn(s1y - 2 * D * cc.y)};
+    return {i2d_rn(s1x - 2 * D * cc.x, eadj), i2d_rn(s1y - 2 * D * cc.y, eadj)};
   }
   const bool wall = near_wall2<D>(idx, f.n);
   long long s2x = 0, s2y = 0;
@@ -325,7 +357,7 @@ __device__ __forceinline__ double2 a_lap_exact(const Field<T>& f, const Acc& acc
       s2y += lo.y + hi.y;
     }
   } else {
-    const longlong2 s2 = exact_s2_wall<T, D>(f, acc, idx, c, pc, Nc, &bad);
+    const longlong2 s2 = exact_s2_wall<T, D>(f, acc, idx, c, pc, Nc, F, &bad);
     s2x = s2.x;
     s2y = s2.y;
   }
@@ -335,7 +367,7 @@ __device__ __forceinline__ double2 a_lap_exact(const Field<T>& f, const Acc& acc
   }
   const long long Sx = 16 * s1x - s2x - 30 * D * cc.x;
   const long long Sy = 16 * s1y - s2y - 30 * D * cc.y;
-  return {i2d_rn(Sx), i2d_rn(Sy)};
+  return {i2d_rn(Sx, eadj), i2d_rn(Sy, eadj)};
 }
 
 // The exact-sum Laplacian at a deep-interior site (no wall within two cells),
@@ -343,6 +375,7 @@ __device__ __forceinline__ double2 a_lap_exact(const Field<T>& f, const Acc& acc
 template <class T, int D, int ORDER, class Acc>
 __device__ __forceinline__ double2 a_lap_exact_deep(const Field<T>& f, const Acc& acc, const int* idx, int64_t c,
                                                     double2 pc, double Ng) {
+  const int eadj = f.F - cur_fix(f);
   const longlong2 cc = acc.fx0();
   bool bad = fbad(cc);
   long long s1x = 0, s1y = 0;
@@ -353,12 +386,14 @@ __device__ __forceinline__ double2 a_lap_exact_deep(const Field<T>& f, const Acc
     s1x += u.x + w.x;
     s1y += u.y + w.y;
   }
+  // out-of-range fallback: the FP64 stencil without the wall branch (no wall is within reach of a deep
+  // site, and a periodic grid has none)
   if constexpr (ORDER == 2) {
     if (bad) {
-      const double2 aL = a_lap_slow<T, D, ORDER>(f, acc, idx, c, pc, Ng * f.cLF);
+      const double2 aL = a_lap_body<T, D, ORDER, Acc, false>(f, acc, idx, c, pc, Ng * f.cLF);
       return {aL.x * f.invcLF, aL.y * f.invcLF};
     }
-    return {i2d_rn(s1x - 2 * D * cc.x), i2d_rn(s1y - 2 * D * cc.y)};
+    return {i2d_rn(s1x - 2 * D * cc.x, eadj), i2d_rn(s1y - 2 * D * cc.y, eadj)};
   }
   long long s2x = 0, s2y = 0;
 #pragma unroll
@@ -369,19 +404,19 @@ __device__ __forceinline__ double2 a_lap_exact_deep(const Field<T>& f, const Acc
     s2y += lo.y + hi.y;
   }
   if (bad) {
-    const double2 aL = a_lap_slow<T, D, ORDER>(f, acc, idx, c, pc, Ng * f.cLF);
+    const double2 aL = a_lap_body<T, D, ORDER, Acc, false>(f, acc, idx, c, pc, Ng * f.cLF);
     return {aL.x * f.invcLF, aL.y * f.invcLF};
   }
   const long long Sx = 16 * s1x - s2x - 30 * D * cc.x;
   const long long Sy = 16 * s1y - s2y - 30 * D * cc.y;
-  return {i2d_rn(Sx), i2d_rn(Sy)};
+  return {i2d_rn(Sx, eadj), i2d_rn(Sy, eadj)};
 }
 
 template <class T, int D>
-__device__ __forceinline__ longlong2 GAcc<T, D>::fx0() const { return fix2(ld2<double>(f.in, c), f.F); }
+__device__ __forceinline__ longlong2 GAcc<T, D>::fx0() const { return fix2(ld2<double>(f.in, c), cur_fix(f)); }
 template <class T, int D>
 __device__ __forceinline__ longlong2 GAcc<T, D>::fx1(int k, int s) const {
-  return fix2(ld2<double>(f.in, c + s * f.st[k]), f.F);
+  return fix2(ld2<double>(f.in, c + s * f.st[k]), cur_fix(f));
 }
 
 // Everything a stage writes, on top of the field it reads.
@@ -391,13 +426,16 @@ struct StageArgs {
   const typename T::C* psin;   // Psi^n in stage precision (stage 1: == f.in)
   typename T::C* ktot;         // K_tot
   typename T::C* out;          // Psi_tmp / Psi_out (stages 1-3); F (stage 0)
-  typename T::M* master;       // Psi^n master, updated in stage 4
+  typename T::M* master;       // where stage 4 writes the master Psi^{n+1}
+  const typename T::M* master_in;   // where stage 4 reads the master Psi^n (== master when updated in place)
   typename T::C* n32;          // PMix: FP32 copy of Psi^{n+1} written in stage 4
   typename T::R dtc;           // dt/2, dt/2, dt, dt/6 for stages 1..4
   double dt6;                  // dt/6 in FP64 (PMix stage 4)
   int stage;                   // 0 = write F only, 1..4 = RK4 stage
   unsigned int* flag;          // bit 0: non-finite Psi
   const typename T::VR* Vs;    // exact-sum stages: V / cLF (nullptr when V is)
+  unsigned int* emax;          // exact-sum stage 4: device word that collects the largest biased exponent of
+                               //   the components of Psi^{n+1} (nullptr otherwise)
   int xwall;                   // 3D tiled path: the shell also owns x in [2, 1 + xwall] and its mirror
                                // (deep-interior kernels start at x = 2 + xwall); 0 by default
 };
@@ -456,14 +494,16 @@ __device__ __forceinline__ PointVals<T> load_point(const StageArgs<T>& A, int64_
   p.v = with_v ? ldv<typename T::R>(G ? A.Vs : A.f.V, i) : typename T::R(0);
   if (st >= 1 && st <= 3) p.pn = A.psin[i];
   if (st >= 2) p.K = A.ktot[i];
-  if (st == 4) p.mst = A.master[i];
+  if (st == 4) p.mst = A.master_in[i];
   return p;
 }
 
 // Apply stage A.stage of Eq. RK4_GPU at site i with k = F.
+// Returns, for stage 4, the largest biased exponent of the components written
+// to the FP64 master (0 otherwise; see StageArgs::emax).
 template <class T, int S = -1>
-__device__ __forceinline__ void rk_apply(const StageArgs<T>& A, int64_t i, typename V2<typename T::R>::t F,
-                                         const PointVals<T>& p) {
+__device__ __forceinline__ unsigned int rk_apply(const StageArgs<T>& A, int64_t i, typename V2<typename T::R>::t F,
+                                                 const PointVals<T>& p) {
   using R = typename T::R;
   using C = typename T::C;
   switch ((S >= 0) ? S : A.stage) {
@@ -492,14 +532,15 @@ __device__ __forceinline__ void rk_apply(const StageArgs<T>& A, int64_t i, typen
       }
       A.master[i] = q;
       if (!(finite_bits(q.x) && finite_bits(q.y))) atomicOr(A.flag, 1u);
-      break;
+      return max(expo_bits(q.x), expo_bits(q.y));
     }
   }
+  return 0u;
 }
 
 template <class T>
-__device__ __forceinline__ void rk_update(const StageArgs<T>& A, int64_t i, typename V2<typename T::R>::t F) {
-  rk_apply<T>(A, i, F, load_point<T>(A, i, false));
+__device__ __forceinline__ unsigned int rk_update(const StageArgs<T>& A, int64_t i, typename V2<typename T::R>::t F) {
+  return rk_apply<T>(A, i, F, load_point<T>(A, i, false));
 }
 
 // Update every boundary site whose b-1 neighbour is the interior site c
@@ -508,12 +549,13 @@ __device__ __forceinline__ void rk_update(const StageArgs<T>& A, int64_t i, type
 // F_b = i N_b Psi_b (L0; in units of cLF on the exact-sum stages, like F_c).
 // Out of line: only sites next to a wall call it.
 template <class T, int D, bool EXACT, class Acc>
-__device__ __forceinline__ void serve_walls(const StageArgs<T>& A, const Acc& acc, const int* idx, int64_t c,
-                                         typename V2<typename T::R>::t pc, typename V2<typename T::R>::t F) {
+__device__ __forceinline__ unsigned int serve_walls(const StageArgs<T>& A, const Acc& acc, const int* idx, int64_t c,
+                                                 typename V2<typename T::R>::t pc, typename V2<typename T::R>::t F) {
   using R = typename T::R;
   using C2 = typename V2<R>::t;
   const Field<T>& f = A.f;
   R theta = R(0);
+  unsigned int ex = 0;
   if (f.bc == BC_MSD) {
     const R m2 = norm2(pc);
     if (m2 > f.tiny) theta = fma(F.y, pc.x, -(F.x * pc.y)) / m2;
@@ -543,16 +585,17 @@ __device__ __forceinline__ void serve_walls(const StageArgs<T>& A, const Acc& ac
       const R Nb = fma(EXACT ? f.sG : f.s, norm2(pb), -ldv<R>(EXACT ? A.Vs : f.V, b));
       Fb = {-Nb * pb.y, Nb * pb.x};
     }
-    rk_update<T>(A, b, Fb);
+    ex = max(ex, rk_update<T>(A, b, Fb));
   }
+  return ex;
 }
 
 // The full per-site work: F at interior site c, its update, and the update of
 // every boundary site whose b-1 neighbour is c.  `p` holds c's pointwise
 // operands (load_point).
 template <class T, int D, int ORDER, bool EXACT, class Acc>
-__device__ __forceinline__ void process_site_pv(const StageArgs<T>& A, const Acc& acc, const int* idx, int64_t c,
-                                                const PointVals<T>& p) {
+__device__ __forceinline__ unsigned int process_site_pv(const StageArgs<T>& A, const Acc& acc, const int* idx,
+                                                        int64_t c, const PointVals<T>& p) {
   using R = typename T::R;
   using C2 = typename V2<R>::t;
   const Field<T>& f = A.f;
@@ -563,17 +606,68 @@ __device__ __forceinline__ void process_site_pv(const StageArgs<T>& A, const Acc
   if constexpr (EXACT) aL = a_lap_exact<T, D, ORDER>(f, acc, idx, c, pc, Nc);
   else aL = a_lap<T, D, ORDER>(f, acc, idx, c, pc, Nc);
   const C2 F = {-fma(Nc, pc.y, aL.y), fma(Nc, pc.x, aL.x)};
-  rk_apply<T>(A, c, F, p);
+  unsigned int ex = rk_apply<T>(A, c, F, p);
 
   bool near = false;
 #pragma unroll
   for (int k = 0; k < D; ++k) near |= (idx[k] == 1) | (idx[k] == f.n[k] - 2);
-  if (near) serve_walls<T, D, EXACT>(A, acc, idx, c, pc, F);
+  if (near) ex = max(ex, serve_walls<T, D, EXACT>(A, acc, idx, c, pc, F));
+  return ex;
 }
 
 template <class T, int D, int ORDER, bool EXACT, class Acc>
-__device__ __forceinline__ void process_site(const StageArgs<T>& A, const Acc& acc, const int* idx, int64_t c) {
-  process_site_pv<T, D, ORDER, EXACT>(A, acc, idx, c, load_point<T, -1, EXACT>(A, c, true));
+__device__ __forceinline__ unsigned int process_site(const StageArgs<T>& A, const Acc& acc, const int* idx,
+                                                     int64_t c) {
+  return process_site_pv<T, D, ORDER, EXACT>(A, acc, idx, c, load_point<T, -1, EXACT>(A, c, true));
+}
+
+// ---------------------------------------------------------------------------
+// Periodic grids (BC_PERIODIC; the boundary the stability analysis of Sec.
+// 3.4 assumes): there are no boundary sites, every site is updated, and the
+// site N[k] along axis k is site 0 again.  Every face neighbour of every site
+// is then an ordinary site, so 2SHOC is the five-point form everywhere (the
+// identity above needs no wall ghosts).
+// ---------------------------------------------------------------------------
+template <class T, int D>
+struct GAccP {
+  using R = typename T::R;
+  using C2 = typename V2<R>::t;
+  const Field<T>& f;
+  int64_t c;
+  int idx[D];
+  __device__ __forceinline__ GAccP(const Field<T>& f_, int64_t c_, const int* idx_) : f(f_), c(c_) {
+#pragma unroll
+    for (int k = 0; k < D; ++k) idx[k] = idx_[k];
+  }
+  // stride offset of s cells (|s| <= 2) along axis k, wrapped into [0, N[k])
+  __device__ __forceinline__ int64_t sh(int k, int s) const {
+    int i = idx[k] + s;
+    i = i < 0 ? i + f.n[k] : (i >= f.n[k] ? i - f.n[k] : i);
+    return (int64_t)(i - idx[k]) * f.st[k];
+  }
+  __device__ __forceinline__ C2 at0() const { return ld2<R>(f.in, c); }
+  __device__ __forceinline__ C2 at1(int k, int s) const { return ld2<R>(f.in, c + sh(k, s)); }
+  __device__ __forceinline__ C2 at2(int k, int s, int j, int t) const { return ld2<R>(f.in, c + sh(k, s) + sh(j, t)); }
+  __device__ __forceinline__ longlong2 fx0() const { return fix2(ld2<double>(f.in, c), cur_fix(f)); }
+  __device__ __forceinline__ longlong2 fx1(int k, int s) const {
+    return fix2(ld2<double>(f.in, c + sh(k, s)), cur_fix(f));
+  }
+};
+
+// F and the stage update at site c (multi-index idx) of a periodic grid.
+template <class T, int D, int ORDER, bool EXACT>
+__device__ __forceinline__ unsigned int process_site_periodic(const StageArgs<T>& A, const int* idx, int64_t c) {
+  using R = typename T::R;
+  using C2 = typename V2<R>::t;
+  const Field<T>& f = A.f;
+  const GAccP<T, D> acc(f, c, idx);
+  const PointVals<T> p = load_point<T, -1, EXACT>(A, c, true);
+  const C2 pc = acc.at0();
+  const R Nc = fma(EXACT ? f.sG : f.s, norm2(pc), -p.v);   // units of cLF on the exact-sum stages
+  C2 aL;
+  if constexpr (EXACT) aL = a_lap_exact_deep<T, D, ORDER>(f, acc, idx, c, pc, Nc);
+  else aL = a_lap_body<T, D, ORDER, GAccP<T, D>, false>(f, acc, idx, c, pc, Nc);
+  return rk_apply<T>(A, c, {-fma(Nc, pc.y, aL.y), fma(Nc, pc.x, aL.x)}, p);
 }
 
 // How a stage is launched: kernel variant, CTA tile, and (3D tiled kernel)

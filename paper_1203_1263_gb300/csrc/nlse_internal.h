@@ -19,12 +19,28 @@ inline void tma_tile_shape(int tile_cfg, int* tx, int* ty) {
   }
 }
 
+// The FP32 form's fused step (two RK4 stages per pass; stage_fused.cuh): A[0..3]
+// are stages 1..4, tm12 / tm34 the TMA descriptors of the passes' inputs
+// (Psi^n, Psi_out) with the fused kernel's box (fused_box below).
+template <int ORDER>
+cudaError_t launch_fused_step(const StageArgs<P32>* A, const void* tm12, const void* tm34, const LaunchCfg& L,
+                              cudaStream_t stream);
+bool fused_grid_ok(int d, const int* n);
+// the fused kernel's TMA box: 64 + 8 complex values by 8 + 8 rows
+constexpr int kFusedBoxX = 2 * (64 + 8), kFusedBoxY = 8 + 8;
+
 cudaError_t launch_mass(const void* psi, bool psi_double, int64_t total, double scale, double* partials,
                         double* result, unsigned int* flag, cudaStream_t stream);
 template <class T, int D, int ORDER>
 cudaError_t launch_energy(const Field<T>& f, double scale, double* partials, double* result, unsigned int* flag,
                           cudaStream_t stream);
 cudaError_t launch_vmax(const void* V, bool v_double, int64_t total, unsigned long long* out, cudaStream_t stream);
+// Exact-sum scale: with psi (complex128, n = 2 x sites components) first the
+// largest exponent of psi into *emax, then *fdev = the fraction bits for it
+// (+ offset) and *emax = 0.  With psi == nullptr only the second part (the
+// exponent was collected by the stage-4 kernels).
+cudaError_t launch_fix_update(const double* psi, int64_t n, unsigned int* emax, int* fdev, int F0, int offset,
+                              cudaStream_t stream);
 cudaError_t launch_round_master(const double2* master, float2* n32, int64_t total, cudaStream_t stream);
 cudaError_t launch_scale_v(const double* V, double s, int64_t n, double* Vs, cudaStream_t stream);
 

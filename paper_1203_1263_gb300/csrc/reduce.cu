@@ -94,6 +94,36 @@ __global__ void __launch_bounds__(256) k_energy(const Field<T> f, double* partia
   if (threadIdx.x == 0) { partials[2 * blockIdx.x] = acc.s; partials[2 * blockIdx.x + 1] = acc.c; }
 }
 
+// Periodic grids: every site counts, neighbours wrap.
+template <class T, int D, int ORDER>
+__global__ void __launch_bounds__(256) k_energy_periodic(const Field<T> f, int64_t total, double* partials,
+                                                         unsigned int* flag) {
+  Neu acc = {0.0, 0.0};
+  bool bad = false;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    int idx[D];
+    int64_t rem = t, c = 0;
+#pragma unroll
+    for (int k = D - 1; k >= 0; --k) {
+      idx[k] = int(rem % f.n[k]);
+      rem /= f.n[k];
+      c += idx[k] * f.st[k];
+    }
+    const double2 pc = ld2<double>(f.in, c);
+    const double m2 = norm2(pc);
+    const double v = ldv<double>(f.V, c);
+    const double Nc = fma(f.s, m2, -v);
+    const GAccP<T, D> ga(f, c, idx);
+    const double2 aL = a_lap_body<T, D, ORDER, GAccP<T, D>, false>(f, ga, idx, c, pc, Nc);
+    const double e = fma(-0.5 * f.s, m2 * m2, fma(v, m2, -fma(pc.x, aL.x, pc.y * aL.y)));
+    bad |= !isfinite(e);
+    nadd(acc, e);
+  }
+  if (bad) atomicOr(flag, 2u);
+  acc = block_reduce(acc);
+  if (threadIdx.x == 0) { partials[2 * blockIdx.x] = acc.s; partials[2 * blockIdx.x + 1] = acc.c; }
+}
+
 // Second pass: one block adds the nb block pairs in a fixed order.
 __global__ void __launch_bounds__(256) k_finish(const double* partials, int nb, double scale, double* result) {
   Neu acc = {0.0, 0.0};
@@ -111,6 +141,41 @@ __global__ void __launch_bounds__(256) k_vmax(const VR* __restrict__ V, int64_t 
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_down_sync(0xffffffffu, m, o));
   if ((threadIdx.x & 31) == 0) atomicMax(out, (unsigned long long)__double_as_longlong(m));
+}
+
+// Largest biased exponent over the components of a complex128 array into *out
+// (exact-sum scale of the current state; *out must start at 0).
+__global__ void __launch_bounds__(256) k_max_expo(const double* __restrict__ v, int64_t n, unsigned int* out) {
+  unsigned int e = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    e = max(e, expo_bits(__ldg(v + i)));
+  emax_commit(out, e);
+}
+
+// Fraction bits of the exact-sum stencil for the state whose largest
+// component has biased exponent E (collected in *emax by k_max_expo or by
+// stage 4): |v| < 2^(E - 1022), so F = 54 - (E - 1022 + 3) = 1073 - E keeps
+// every component below 2^(54 - F) with 8x headroom.  A zero state keeps F0;
+// a non-finite one keeps the previous F (the non-finite flag reports it).
+// `offset` is a test hook (nlse_debug_set).  Resets *emax for the next step.
+__global__ void k_fix_update(unsigned int* emax, int* fdev, int F0, int offset) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    const unsigned int E = *emax;
+    if (E == 0u) *fdev = F0 + offset;
+    else if (E < 2047u) *fdev = 1073 - int(E) + offset;
+    *emax = 0u;
+  }
+}
+
+cudaError_t launch_fix_update(const double* psi, int64_t n, unsigned int* emax, int* fdev, int F0, int offset,
+                              cudaStream_t stream) {
+  if (psi) {
+    int64_t b = (n + 255) / 256;
+    if (b > 152 * 8) b = 152 * 8;
+    k_max_expo<<<(unsigned)b, 256, 0, stream>>>(psi, n, emax);
+  }
+  k_fix_update<<<1, 32, 0, stream>>>(emax, fdev, F0, offset);
+  return cudaGetLastError();
 }
 
 static int reduce_blocks(int64_t work) {
@@ -132,6 +197,14 @@ cudaError_t launch_mass(const void* psi, bool psi_double, int64_t total, double 
 template <class T, int D, int ORDER>
 cudaError_t launch_energy(const Field<T>& f, double scale, double* partials, double* result, unsigned int* flag,
                           cudaStream_t stream) {
+  if (f.bc == BC_PERIODIC) {
+    int64_t total = 1;
+    for (int k = 0; k < D; ++k) total *= f.n[k];
+    const int nb = reduce_blocks(total);
+    k_energy_periodic<T, D, ORDER><<<nb, 256, 0, stream>>>(f, total, partials, flag);
+    k_finish<<<1, 256, 0, stream>>>(partials, nb, scale, result);
+    return cudaGetLastError();
+  }
   const int nb = reduce_blocks(f.ninterior);
   k_energy<T, D, ORDER><<<nb, 256, 0, stream>>>(f, partials, flag);
   k_finish<<<1, 256, 0, stream>>>(partials, nb, scale, result);

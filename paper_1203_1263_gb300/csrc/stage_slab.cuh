@@ -100,19 +100,22 @@ __global__ void __launch_bounds__(SlabShape<NS>::THREADS) k_stage_slab(const Sta
   // operands share 32-byte sectors)
   const int tn = tid % NS, tf = (tid / NS) % kSlabTF, tm = tid / (NS * kSlabTF);
   const int fs = f0 + tf, ms = m0 + tm, ns = n_first + tn;
-  if (fs > rg.f_hi || ms > rg.m_hi) return;
-  int idx[3];
-  idx[AXM] = ms;
-  idx[AXN] = ns;
-  idx[AXF] = fs;
-  const int64_t c = (int64_t)idx[0] * f.st[0] + (int64_t)idx[1] * f.st[1] + (int64_t)idx[2] * f.st[2];
-  SlabAcc<T, AXM, AXN, AXF> acc;
+  unsigned int ex = 0;
+  if (fs <= rg.f_hi && ms <= rg.m_hi) {
+    int idx[3];
+    idx[AXM] = ms;
+    idx[AXN] = ns;
+    idx[AXF] = fs;
+    const int64_t c = (int64_t)idx[0] * f.st[0] + (int64_t)idx[1] * f.st[1] + (int64_t)idx[2] * f.st[2];
+    SlabAcc<T, AXM, AXN, AXF> acc;
 #pragma unroll
-  for (int k = 0; k < 5; ++k) acc.p[k] = win + (tm + k) * PL;
-  acc.wf = WF;
-  acc.o = (ns - n_win0) * WF + (tf + 2);
-  acc.F = f.F;
-  process_site<T, 3, ORDER, EXACT>(A, acc, idx, c);
+    for (int k = 0; k < 5; ++k) acc.p[k] = win + (tm + k) * PL;
+    acc.wf = WF;
+    acc.o = (ns - n_win0) * WF + (tf + 2);
+    acc.F = EXACT ? cur_fix(f) : 0;
+    ex = process_site<T, 3, ORDER, EXACT>(A, acc, idx, c);
+  }
+  if (A.emax) emax_commit(A.emax, ex);
 }
 
 inline bool slab_ok(const int* n) { return n[0] >= 7 && n[1] >= 7 && n[2] >= 10; }

@@ -101,6 +101,8 @@ __global__ void __launch_bounds__(TX* TY) k_stage3d_tiled(const StageArgs<T> A, 
   const int zb = 1 + blockIdx.z * zc;
   const int ze = min(zb + zc, nz - 1);   // planes [zb, ze) are computed
   const int64_t plane = (int64_t)ny * nx;
+  const int F = EXACT ? cur_fix(f) : 0;
+  unsigned int ex = 0;
 
   E regs[NPER];
   auto load = [&](int z) {
@@ -110,7 +112,7 @@ __global__ void __launch_bounds__(TX* TY) k_stage3d_tiled(const StageArgs<T> A, 
       const int r = e / W, q = e - r * W;
       const int gy = y0 - 2 + r, gx = x0 - 2 + q;
       const bool ok = e < PS && z >= 0 && z < nz && gy >= 0 && gy < ny && gx >= 0 && gx < nx;
-      regs[i] = ring_value<EXACT, C, E>(ok ? f.in[z * plane + (int64_t)gy * nx + gx] : C{0, 0}, f.F);
+      regs[i] = ring_value<EXACT, C, E>(ok ? f.in[z * plane + (int64_t)gy * nx + gx] : C{0, 0}, F);
     }
   };
   auto store = [&](int z) {
@@ -146,7 +148,7 @@ __global__ void __launch_bounds__(TX* TY) k_stage3d_tiled(const StageArgs<T> A, 
         const auto pc = acc.at0();
         const auto Nc = fma(f.sG, norm2(pc), -pv.v);   // units of cLF
         const auto aL = a_lap_exact_deep<T, 3, ORDER>(f, acc, idx, c, pc, Nc);
-        rk_apply<T>(A, c, {-fma(Nc, pc.y, aL.y), fma(Nc, pc.x, aL.x)}, pv);
+        ex = max(ex, rk_apply<T>(A, c, {-fma(Nc, pc.y, aL.y), fma(Nc, pc.x, aL.x)}, pv));
       } else {
         SAcc3<T> acc;
 #pragma unroll
@@ -164,6 +166,7 @@ __global__ void __launch_bounds__(TX* TY) k_stage3d_tiled(const StageArgs<T> A, 
     if (z + 4 <= ze + 1) load(z + 4);
     __syncthreads();
   }
+  if (A.emax) emax_commit(A.emax, ex);
 }
 
 template <class T, int ORDER, int TX, int TY, bool EXACT>
@@ -179,6 +182,8 @@ __global__ void __launch_bounds__(TX* TY) k_stage2d_tiled(const StageArgs<T> A) 
   const int gx = x0 + threadIdx.x, gy = y0 + threadIdx.y;
   const bool deep = gx >= 2 && gx <= nx - 3 && gy >= 2 && gy <= ny - 3;   // wall shell: shell kernel
   const int64_t c = (int64_t)gy * nx + gx;
+  const int F = EXACT ? cur_fix(f) : 0;
+  unsigned int ex = 0;
   PointVals<T> pv;   // requested before the tile, so that both latencies overlap
   if (deep) pv = load_point<T, -1, EXACT>(A, c, f.V != nullptr);
 #pragma unroll
@@ -188,7 +193,7 @@ __global__ void __launch_bounds__(TX* TY) k_stage2d_tiled(const StageArgs<T> A) 
       const int r = e / W, q = e - r * W;
       const int ty_ = y0 - 2 + r, tx_ = x0 - 2 + q;
       tile[e] = ring_value<EXACT, C, E>((ty_ >= 0 && ty_ < ny && tx_ >= 0 && tx_ < nx) ? f.in[(int64_t)ty_ * nx + tx_]
-                                                                                       : C{0, 0}, f.F);
+                                                                                       : C{0, 0}, F);
     }
   }
   __syncthreads();
@@ -202,7 +207,7 @@ __global__ void __launch_bounds__(TX* TY) k_stage2d_tiled(const StageArgs<T> A) 
       const auto pc = acc.at0();
       const auto Nc = fma(f.sG, norm2(pc), -pv.v);   // units of cLF
       const auto aL = a_lap_exact_deep<T, 2, ORDER>(f, acc, idx, c, pc, Nc);
-      rk_apply<T>(A, c, {-fma(Nc, pc.y, aL.y), fma(Nc, pc.x, aL.x)}, pv);
+      ex = rk_apply<T>(A, c, {-fma(Nc, pc.y, aL.y), fma(Nc, pc.x, aL.x)}, pv);
     } else {
       SAcc2<T> acc;
       acc.p = tile;
@@ -214,6 +219,7 @@ __global__ void __launch_bounds__(TX* TY) k_stage2d_tiled(const StageArgs<T> A) 
       rk_apply<T>(A, c, {-fma(Nc, pc.y, aL.y), fma(Nc, pc.x, aL.x)}, pv);
     }
   }
+  if (A.emax) emax_commit(A.emax, ex);
 }
 
 // Tile shapes selectable at run time (tile_cfg); -1 picks the default.

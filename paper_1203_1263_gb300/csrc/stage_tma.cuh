@@ -220,7 +220,8 @@ __global__ void __launch_bounds__(TX* TYT, 3) k_stage3d_tma_exact(const StageArg
   const int jb = zb - 2, jl = ze + 1;
   const int64_t plane = (int64_t)ny * nx;
   const bool with_v = f.V != nullptr;
-  const int F = f.F;
+  const int F = cur_fix(f), eadj = f.F - F;   // this step's fixed-point scale, and its shift to units of cLF
+  unsigned int ex = 0;
 
   if (tid == 0) {
     for (int s = 0; s < RD; ++s) mbar_init(smem_u32(bars + s), 1);
@@ -334,14 +335,14 @@ __global__ void __launch_bounds__(TX* TYT, 3) k_stage3d_tma_exact(const StageArg
       const double Nc = fma(f.sG, norm2(pc), -pv[r].v);
       double2 aL;
       if (!bad) {
-        aL = {i2d_rn(Sx), i2d_rn(Sy)};
+        aL = {i2d_rn(Sx, eadj), i2d_rn(Sy, eadj)};
       } else {   // an operand out of the fixed-point range: the FP64 stencil from global memory
         const int idx[3] = {z, gy[r], gx};
         const GAcc<T, 3> ga(f, c);
         aL = a_lap_slow<T, 3, ORDER>(f, ga, idx, c, pc, Nc * f.cLF);
         aL = {aL.x * f.invcLF, aL.y * f.invcLF};
       }
-      rk_apply<T, S>(A, c, {-fma(Nc, pc.y, aL.y), fma(Nc, pc.x, aL.x)}, pv[r]);
+      ex = max(ex, rk_apply<T, S>(A, c, {-fma(Nc, pc.y, aL.y), fma(Nc, pc.x, aL.x)}, pv[r]));
     }
     if (__syncthreads_or(late)) {
       aborted = true;
@@ -350,6 +351,7 @@ __global__ void __launch_bounds__(TX* TYT, 3) k_stage3d_tma_exact(const StageArg
     fz = (fz + 1 == RF) ? 0 : fz + 1;
     if (tid == 0 && issued < jl) issue(issued + 1);
   }
+  if (S == 4 && A.emax) emax_commit(A.emax, ex);
   if (aborted && tid == 0) {
     atomicOr(A.flag, kFlagTimeout);
     for (int j = max(jb, issued - RD + 1); j <= issued; ++j) {

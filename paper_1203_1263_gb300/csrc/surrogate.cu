@@ -1093,6 +1093,94 @@ __global__ void k_state_mass(const float2* __restrict__ in, const float2* __rest
   }
 }
 
+// Per-state sums of |psi + y|^2 (the network's raw output, y with a pc-channel row stride) and
+// |target|^2, in the layout of k_state_mass.
+__global__ void k_state_mass_res(const float2* __restrict__ psi, const float* __restrict__ y, int pc,
+                                 const float2* __restrict__ target, int64_t HW, double* __restrict__ part) {
+  __shared__ double r0[256], r1[256];
+  const int64_t base = (int64_t)blockIdx.y * HW;
+  double a = 0.0, b = 0.0;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < HW; p += (int64_t)gridDim.x * blockDim.x) {
+    const float2 u = psi[base + p], t = target[base + p];
+    const float2 d = *reinterpret_cast<const float2*>(y + (base + p) * pc);
+    const float ox = u.x + d.x, oy = u.y + d.y;
+    a += double(ox) * ox + double(oy) * oy;
+    b += double(t.x) * t.x + double(t.y) * t.y;
+  }
+  r0[threadIdx.x] = a;
+  r1[threadIdx.x] = b;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) {
+      r0[threadIdx.x] += r0[threadIdx.x + o];
+      r1[threadIdx.x] += r1[threadIdx.x + o];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    part[((int64_t)blockIdx.y * kMassBlocks + blockIdx.x) * 2] = r0[0];
+    part[((int64_t)blockIdx.y * kMassBlocks + blockIdx.x) * 2 + 1] = r1[0];
+  }
+}
+
+// Per-state sums of |a - b|^2 and |b|^2, in the layout of k_state_mass.
+__global__ void k_state_diff(const float2* __restrict__ a_, const float2* __restrict__ b_, int64_t HW,
+                             double* __restrict__ part) {
+  __shared__ double r0[256], r1[256];
+  const int64_t base = (int64_t)blockIdx.y * HW;
+  double a = 0.0, b = 0.0;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < HW; p += (int64_t)gridDim.x * blockDim.x) {
+    const float2 u = a_[base + p], v = b_[base + p];
+    const double dx = double(u.x) - v.x, dy = double(u.y) - v.y;
+    a += dx * dx + dy * dy;
+    b += double(v.x) * v.x + double(v.y) * v.y;
+  }
+  r0[threadIdx.x] = a;
+  r1[threadIdx.x] = b;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) {
+      r0[threadIdx.x] += r0[threadIdx.x + o];
+      r1[threadIdx.x] += r1[threadIdx.x + o];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    part[((int64_t)blockIdx.y * kMassBlocks + blockIdx.x) * 2] = r0[0];
+    part[((int64_t)blockIdx.y * kMassBlocks + blockIdx.x) * 2 + 1] = r1[0];
+  }
+}
+
+// out2[2b], out2[2b + 1]: the two per-state sums, partials added in a fixed order (one thread per state)
+__global__ void k_state_sums(const double* __restrict__ part, int nb, double* __restrict__ out2) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= nb) return;
+  double a = 0.0, c = 0.0;
+  for (int i = 0; i < kMassBlocks; ++i) {
+    a += part[((int64_t)b * kMassBlocks + i) * 2];
+    c += part[((int64_t)b * kMassBlocks + i) * 2 + 1];
+  }
+  out2[2 * b] = a;
+  out2[2 * b + 1] = c;
+}
+
+// The mass term of the loss, mu mean_b delta_b^2 with delta_b = (M_out - M_t) / M_t: per state the
+// coefficient of its gradient, d/d out = coef_b out with coef_b = 4 mu delta_b / (nb M_t), and the
+// term itself into *loss (one thread per state).
+__global__ void k_mass_coef(const double* __restrict__ part, int nb, double mu, double* __restrict__ coef,
+                            double* __restrict__ loss) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= nb) return;
+  double mo = 0.0, mt = 0.0;
+  for (int i = 0; i < kMassBlocks; ++i) {
+    mo += part[((int64_t)b * kMassBlocks + i) * 2];
+    mt += part[((int64_t)b * kMassBlocks + i) * 2 + 1];
+  }
+  const double delta = mt > 0.0 ? (mo - mt) / mt : 0.0;
+  coef[b] = mt > 0.0 ? 4.0 * mu * delta / (double(nb) * mt) : 0.0;
+  atomicAdd(loss, mu * delta * delta / double(nb));
+}
+
 // out *= sqrt(M_in / M_out) per state (same grid as k_state_mass; partials summed in a fixed order)
 __global__ void k_project(float2* __restrict__ out, int64_t HW, const double* __restrict__ part) {
   __shared__ float r;
@@ -1219,8 +1307,10 @@ __global__ void k_residual(const float2* __restrict__ psi, const float* __restri
 // MSE loss (FP64 partial sums) and its gradient w.r.t. y, written as the BF16
 // output gradient of the last layer (pc-channel rows, channels 2.. zero); one
 // thread per 16-byte chunk of that gradient
+// With coef (the mass term, k_mass_coef), coef[p / HW] psi_out[p] is added to the gradient.
 __global__ void k_mse(const float2* __restrict__ psi, const float* __restrict__ y, const float2* __restrict__ target,
-                      int64_t P, int pc, bf16* __restrict__ dz, double* __restrict__ loss_acc) {
+                      int64_t P, int pc, bf16* __restrict__ dz, double* __restrict__ loss_acc,
+                      const double* __restrict__ coef, int64_t HW) {
   __shared__ double red[256];
   double s = 0.0;
   const float scale = 2.f / float(2 * P);
@@ -1234,7 +1324,13 @@ __global__ void k_mse(const float2* __restrict__ psi, const float* __restrict__ 
       const float2 d = *reinterpret_cast<const float2*>(y + p * pc);
       const float ex = u.x + d.x - t.x, ey = u.y + d.y - t.y;
       s += double(ex) * ex + double(ey) * ey;
-      const __nv_bfloat162 g = __floats2bfloat162_rn(scale * ex, scale * ey);
+      float gx = scale * ex, gy = scale * ey;
+      if (coef) {
+        const float cb = float(coef[p / HW]);
+        gx = fmaf(cb, u.x + d.x, gx);
+        gy = fmaf(cb, u.y + d.y, gy);
+      }
+      const __nv_bfloat162 g = __floats2bfloat162_rn(gx, gy);
       v.x = *reinterpret_cast<const uint32_t*>(&g);
     }
     dst[q] = v;
@@ -1363,6 +1459,8 @@ struct nlse_sur {
   float* m2;
   double* loss;
   double* mass_part;              // [max_batch][kMassBlocks][2]
+  double* mstat;                  // [2 max_batch]: the mass term's gradient coefficients, or per-state sum pairs
+  double mass_weight;             // weight of the mass term in the loss (0: plain MSE)
   float* amax_part;               // [max_batch][kMassBlocks]
   float2* xnoisy;                 // noisy training input [max_batch][H][W]
   uint64_t seed;
@@ -1410,6 +1508,7 @@ size_t ws_bytes(int H, int W, int C, int L, int max_batch) {
   off = al(off + np * 4);            // m2
   off = al(off + 64);                // loss
   off = al(off + (size_t)max_batch * kMassBlocks * 2 * 8);   // mass_part
+  off = al(off + (size_t)max_batch * 2 * 8);                  // mstat
   off = al(off + (size_t)max_batch * kMassBlocks * 4);       // amax_part
   off = al(off + P * 8);                                      // xnoisy
   off = al(off + 16);                // err
@@ -1637,7 +1736,14 @@ cudaError_t backward(const nlse_sur* s, int nb, const float2* psi_in, const floa
   if (e == cudaSuccess) e = cudaMemsetAsync(s->loss, 0, sizeof(double), s->stream);
   if (e != cudaSuccess) return e;
   bf16* dz = s->dzA;   // gradient w.r.t. the current layer's pre-activation
-  k_mse<<<grid1d(P * s->pc / 8), 256, 0, s->stream>>>(psi_in, s->y, target, P, s->pc, dz, s->loss);
+  const int64_t HW = (int64_t)s->H * s->W;
+  if (s->mass_weight > 0.0) {
+    k_state_mass_res<<<dim3(kMassBlocks, (unsigned)nb), 256, 0, s->stream>>>(psi_in, s->y, s->pc, target, HW,
+                                                                             s->mass_part);
+    k_mass_coef<<<(nb + 31) / 32, 32, 0, s->stream>>>(s->mass_part, nb, s->mass_weight, s->mstat, s->loss);
+  }
+  k_mse<<<grid1d(P * s->pc / 8), 256, 0, s->stream>>>(psi_in, s->y, target, P, s->pc, dz, s->loss,
+                                                      s->mass_weight > 0.0 ? s->mstat : nullptr, HW);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   for (int l = s->L - 1; l >= 0 && e == cudaSuccess; --l) {
     const bool first = l == 0, last = l == s->L - 1;
@@ -1734,6 +1840,8 @@ int nlse_sur_create(nlse_sur_t* out, int H, int W, int channels, int layers, con
   s->m2 = (float*)(base + o); o = al(o + s->nparam * 4);
   s->loss = (double*)(base + o); o = al(o + 64);
   s->mass_part = (double*)(base + o); o = al(o + (size_t)max_batch * kMassBlocks * 2 * 8);
+  s->mstat = (double*)(base + o); o = al(o + (size_t)max_batch * 2 * 8);
+  s->mass_weight = 0.0;
   s->amax_part = (float*)(base + o); o = al(o + (size_t)max_batch * kMassBlocks * 4);
   s->xnoisy = (float2*)(base + o); o = al(o + P * 8);
   s->err = (int*)(base + o); o = al(o + 16);
@@ -1804,7 +1912,7 @@ int nlse_sur_sync_params(nlse_sur_t s) {
   return e == cudaSuccess ? NLSE_OK : sfail(NLSE_ECUDA, cudaGetErrorString(e));
 }
 
-int nlse_sur_forward(nlse_sur_t s, int nb, const void* psi_in, void* psi_out, int project_mass) {
+int nlse_sur_forward(nlse_sur_t s, int nb, const void* psi_in, void* psi_out, int project_mass, double* masses_out) {
   if (!s || !psi_in || !psi_out) return sfail(NLSE_EINVAL, "NULL argument");
   if (nb < 1 || nb > s->max_batch) return sfail(NLSE_EINVAL, "batch outside 1..max_batch");
   cudaError_t e = forward(s, nb, (const float2*)psi_in, false);
@@ -1813,14 +1921,40 @@ int nlse_sur_forward(nlse_sur_t s, int nb, const void* psi_in, void* psi_out, in
     k_residual<<<grid1d(P), 256, 0, s->stream>>>((const float2*)psi_in, s->y, P, s->pc, (float2*)psi_out);
     e = cudaGetLastError();
   }
-  if (e == cudaSuccess && project_mass) {
+  if (e == cudaSuccess && (project_mass || masses_out)) {
     const int64_t HW = (int64_t)s->H * s->W;
     const dim3 grid(kMassBlocks, (unsigned)nb);
     k_state_mass<<<grid, 256, 0, s->stream>>>((const float2*)psi_in, (const float2*)psi_out, HW, s->mass_part);
-    k_project<<<grid, 256, 0, s->stream>>>((float2*)psi_out, HW, s->mass_part);
+    if (masses_out) k_state_sums<<<(nb + 31) / 32, 32, 0, s->stream>>>(s->mass_part, nb, masses_out);
+    if (project_mass) k_project<<<grid, 256, 0, s->stream>>>((float2*)psi_out, HW, s->mass_part);
     e = cudaGetLastError();
   }
   return e == cudaSuccess ? NLSE_OK : sfail(NLSE_ECUDA, cudaGetErrorString(e));
+}
+
+int nlse_sur_set_mass_weight(nlse_sur_t s, double mass_weight) {
+  if (!s) return sfail(NLSE_EINVAL, "NULL surrogate");
+  if (!(mass_weight >= 0.0) || !isfinite(mass_weight)) return sfail(NLSE_EINVAL, "mass weight must be >= 0");
+  s->mass_weight = mass_weight;
+  return NLSE_OK;
+}
+
+int nlse_sur_compare(nlse_sur_t s, int nb, const void* a, const void* b, double* rel_l2_host) {
+  if (!s || !a || !b || !rel_l2_host) return sfail(NLSE_EINVAL, "NULL argument");
+  if (nb < 1 || nb > s->max_batch) return sfail(NLSE_EINVAL, "batch outside 1..max_batch");
+  const int64_t HW = (int64_t)s->H * s->W;
+  k_state_diff<<<dim3(kMassBlocks, (unsigned)nb), 256, 0, s->stream>>>((const float2*)a, (const float2*)b, HW,
+                                                                       s->mass_part);
+  k_state_sums<<<(nb + 31) / 32, 32, 0, s->stream>>>(s->mass_part, nb, s->mstat);
+  cudaError_t e = cudaGetLastError();
+  std::vector<double> sums(2 * (size_t)nb);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(sums.data(), s->mstat, sizeof(double) * 2 * nb, cudaMemcpyDeviceToHost,
+                                            s->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) return sfail(NLSE_ECUDA, cudaGetErrorString(e));
+  for (int i = 0; i < nb; ++i)
+    rel_l2_host[i] = sums[2 * i + 1] > 0.0 ? sqrt(sums[2 * i] / sums[2 * i + 1]) : (sums[2 * i] > 0.0 ? INFINITY : 0.0);
+  return NLSE_OK;
 }
 
 int nlse_sur_gradients(nlse_sur_t s, int nb, const void* psi_in, const void* psi_target, float* grad_out,

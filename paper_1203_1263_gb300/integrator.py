@@ -84,6 +84,10 @@ class Integrator:
     def step(self, nsteps: int, dt: float) -> None:
         L.check(self.lib.nlse_step(self.ctx, int(nsteps), float(dt)))
 
+    def refresh_potential(self) -> None:
+        """Re-read self.V after writing new values into it (nlse_refresh_potential)."""
+        L.check(self.lib.nlse_refresh_potential(self.ctx))
+
     def mass(self) -> float:
         out = ctypes.c_double()
         L.check(self.lib.nlse_mass(self.ctx, ctypes.byref(out)))
@@ -107,6 +111,12 @@ class Integrator:
 
     def set_kernel(self, variant: int, tile_cfg: int = -1) -> None:
         L.check(self.lib.nlse_set_kernel(self.ctx, int(variant), int(tile_cfg)))
+
+    def kernel_in_use(self) -> int:
+        """The stage kernel variant the graph-replayed steps run with (nlse_kernel_in_use)."""
+        v = int(self.lib.nlse_kernel_in_use(self.ctx))
+        L.check(min(v, 0))
+        return v
 
     def autotune(self):
         """Pick the fastest tile shape for this problem (see nlse_autotune); returns (tile_cfg, ms)."""

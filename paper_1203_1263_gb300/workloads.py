@@ -347,7 +347,7 @@ def humps_2d(seed: int, index: int, n: int = 256, h: float = 0.2):
     return psi
 
 
-def random_field(shape, seed: int, smooth: bool = False) -> np.ndarray:
+def random_field(shape, seed: int) -> np.ndarray:
     """Complex field with i.i.d. U[-1, 1) parts (parity tests on small grids)."""
     n = int(np.prod(shape))
     u = uniform(seed, 2 * n)

@@ -50,7 +50,7 @@ def test_workspace_bytes():
 
 @pytest.mark.parametrize("args,code", [
     (dict(dims=0), L.NLSE_EINVAL), (dict(N=[2, 5, 5]), L.NLSE_EINVAL), (dict(h=0.0), L.NLSE_EINVAL),
-    (dict(a=-1.0), L.NLSE_EINVAL), (dict(order=3), L.NLSE_EINVAL), (dict(bc=5), L.NLSE_EINVAL), (dict(bc=3), L.NLSE_EINVAL),
+    (dict(a=-1.0), L.NLSE_EINVAL), (dict(order=3), L.NLSE_EINVAL), (dict(bc=5), L.NLSE_EINVAL), (dict(bc=4), L.NLSE_EINVAL),
     (dict(dtype=9), L.NLSE_EINVAL), (dict(psi=None), L.NLSE_EINVAL), (dict(ws=None), L.NLSE_EINVAL),
     (dict(ws_bytes=16), L.NLSE_ENOMEM), (dict(ws=4096 + 8), L.NLSE_EINVAL),
 ])
@@ -86,3 +86,14 @@ def test_batch_workspace_accepts_every_boundary(bc):
 def test_batch_workspace_rejects_bad_runs(bad):
     runs = (L.RunDesc * 2)(_run(), _run(**bad))
     assert L.lib().nlse_batch_workspace_bytes(2, runs) == 0
+
+
+@pytest.mark.parametrize("n", [[4, 2 ** 62 + 1], [512, 512, 129], [2 ** 31, 2 ** 31, 2 ** 31]])
+def test_noalloc_rejects_oversized_grids_before_touching_the_gpu(n):
+    """The site count is checked against the scratch limit before each
+    multiplication, so extents whose product overflows int64 are rejected
+    too, with the limit in the message."""
+    lib = L.lib()
+    rc = lib.nlse_mass_noalloc(len(n), L.int64_array(n), 0.1, L.C128, 4096, 4096, None)
+    assert rc == L.NLSE_EINVAL
+    assert b"maximum of 33554432 sites" in lib.nlse_last_error()

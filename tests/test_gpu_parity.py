@@ -19,7 +19,7 @@ from paper_1203_1263_gb300.integrator import Integrator
 pytestmark = pytest.mark.gpu
 
 TOL = {"c128": (1e-12, 1e-11), "c64": (2e-5, 2e-4), "c64_acc64": (2e-5, 2e-4)}
-BCS = {"dirichlet": W.BC_DIRICHLET, "msd": W.BC_MSD, "l0": W.BC_L0}
+BCS = {"dirichlet": W.BC_DIRICHLET, "msd": W.BC_MSD, "l0": W.BC_L0, "periodic": W.BC_PERIODIC}
 
 SHAPES = {
     1: [(37,), (3,), (4,), (1000,)],
@@ -53,6 +53,14 @@ def field(shape, seed):
     return ((1 + 0.3 * win * r.real) * np.exp(1j * r.imag)).astype(np.complex128)
 
 
+def periodic_field(shape, seed):
+    """Smooth periodic structure with no window: the values on either side of
+    the wrap differ, so a wrong wrap shows."""
+    r = _smooth(W.random_field(shape, seed), 3)
+    r = r / np.max(np.abs(r))
+    return ((1 + 0.3 * r.real) * np.exp(1j * r.imag)).astype(np.complex128)
+
+
 def compare(got, ref, dtype):
     rl2, elem = TOL[dtype]
     got = np.asarray(got, dtype=np.complex128)
@@ -62,8 +70,8 @@ def compare(got, ref, dtype):
     return err
 
 
-def problem(shape, seed, with_v=True):
-    psi = field(shape, seed)
+def problem(shape, seed, with_v=True, bc="dirichlet"):
+    psi = periodic_field(shape, seed) if bc == "periodic" else field(shape, seed)
     V = W.random_potential(shape, seed + 1, 0.5) if with_v else None
     return psi, V
 
@@ -84,12 +92,12 @@ def oracle_rk4_cached(key, *args):
 
 @pytest.mark.parametrize("dims,shape", CASES)
 @pytest.mark.parametrize("order", [2, 4])
-@pytest.mark.parametrize("bc", ["dirichlet", "msd", "l0"])
+@pytest.mark.parametrize("bc", ["dirichlet", "msd", "l0", "periodic"])
 @pytest.mark.parametrize("dtype", ["c128", "c64", "c64_acc64"])
-@pytest.mark.parametrize("variant", [0, 1, 2, 3])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4])
 def test_step_matches_oracle(dims, shape, order, bc, dtype, variant):
     h, a, s = 0.35, 0.8, -1.1
-    psi, V = problem(shape, 100 + dims * 10 + order)
+    psi, V = problem(shape, 100 + dims * 10 + order, bc=bc)
     dt = stable_dt(shape, h, a, s, order, V)
     nsteps = 21   # one graph replay of 16 steps + 5 single steps
     ref = oracle_rk4_cached((shape, order, bc), psi, h, a, s, dt, nsteps, V, BCS[bc], order)
@@ -102,11 +110,11 @@ def test_step_matches_oracle(dims, shape, order, bc, dtype, variant):
 
 @pytest.mark.parametrize("dims,shape", [(1, (37,)), (2, (19, 45)), (3, (9, 21, 70)), (3, (3, 4, 5))])
 @pytest.mark.parametrize("order", [2, 4])
-@pytest.mark.parametrize("bc", ["dirichlet", "msd", "l0"])
+@pytest.mark.parametrize("bc", ["dirichlet", "msd", "l0", "periodic"])
 @pytest.mark.parametrize("dtype", ["c128", "c64"])
 def test_rhs_matches_oracle(dims, shape, order, bc, dtype):
     h, a, s = 0.3, 0.9, 1.3
-    psi, V = problem(shape, 7 + dims)
+    psi, V = problem(shape, 7 + dims, bc=bc)
     ref = O.evalF(psi, h, a, s, V, BCS[bc], order)
     g = Integrator(psi, h, a, s, V, bc, order, dtype)
     got = g.rhs().cpu().numpy()
@@ -116,11 +124,11 @@ def test_rhs_matches_oracle(dims, shape, order, bc, dtype):
 
 @pytest.mark.parametrize("dims,shape", [(1, (1000,)), (2, (70, 33)), (3, (20, 17, 64))])
 @pytest.mark.parametrize("order", [2, 4])
-@pytest.mark.parametrize("bc", ["dirichlet", "msd", "l0"])
+@pytest.mark.parametrize("bc", ["dirichlet", "msd", "l0", "periodic"])
 @pytest.mark.parametrize("dtype", ["c128", "c64", "c64_acc64"])
 def test_mass_energy_match_oracle(dims, shape, order, bc, dtype):
     h, a, s = 0.25, 0.7, -0.6
-    psi, V = problem(shape, 55)
+    psi, V = problem(shape, 55, bc=bc)
     g = Integrator(psi, h, a, s, V, bc, order, dtype)
     # the oracle sees exactly what the GPU holds (FP32 forms: the rounded state and potential)
     held = g.numpy().astype(np.complex128)
@@ -155,8 +163,8 @@ def test_tiled_kernel_equals_generic_bitwise(dtype, dims, shape, tile_cfg):
     """The tiled kernels perform the generic kernel's arithmetic in the same
     order; only where the operands come from differs."""
     for order in (2, 4):
-        for bc in ("dirichlet", "msd", "l0"):
-            psi, V = problem(shape, 77)
+        for bc in ("dirichlet", "msd", "l0", "periodic"):
+            psi, V = problem(shape, 77, bc=bc)
             h, a, s = 0.3, 0.6, -1.0
             dt = stable_dt(shape, h, a, s, order, V)
             res = []
@@ -169,23 +177,90 @@ def test_tiled_kernel_equals_generic_bitwise(dtype, dims, shape, tile_cfg):
             assert np.array_equal(res[2], res[3]), (order, bc)
 
 
-@pytest.mark.parametrize("bc", ["dirichlet", "l0"])
+FUSED_SHAPES = [(16, 16, 16), (20, 24, 70), (33, 40, 64), (40, 37, 130), (18, 70, 66), (20, 24, 71)]
+
+
+@pytest.mark.parametrize("shape", FUSED_SHAPES)
+@pytest.mark.parametrize("bc", ["dirichlet", "msd", "l0", "periodic"])
+@pytest.mark.parametrize("order", [2, 4])
+@pytest.mark.parametrize("with_v", [True, False])
+def test_fused_step_equals_stage_streaming_bitwise(shape, bc, order, with_v):
+    """Two stages per pass (variant 4) against one pass per stage (variant 1),
+    FP32: 37 steps (two graph-replayed chunks of 16 fused steps with the
+    Psi ping-pong, then 5 single steps) give the same bits; odd Nx and
+    periodic grids run the stage-streaming path."""
+    psi, V = problem(shape, 61, with_v=with_v, bc=bc)
+    h, a, s = 0.3, 0.6, -1.0
+    dt = stable_dt(shape, h, a, s, order, V)
+    res = []
+    for variant in (1, 4):
+        g = Integrator(psi, h, a, s, V, bc, order, "c64")
+        g.set_kernel(variant)
+        assert g.kernel_in_use() == (4 if variant == 4 and shape[2] % 2 == 0 and bc != "periodic" else 1)
+        g.step(37, dt)
+        g.sync()
+        res.append(g.numpy())
+    assert np.array_equal(res[0], res[1])
+    compare(res[1], O.rk4(psi, h, a, s, dt, 37, V, BCS[bc], order), "c64")
+
+
+@pytest.mark.parametrize("bc", ["dirichlet", "msd", "l0", "periodic"])
+@pytest.mark.parametrize("variant", [2, 3])
+@pytest.mark.parametrize("dims,shape", [(1, (37,)), (2, (19, 45)), (3, (9, 21, 70))])
+@pytest.mark.parametrize("factor", [1e2, 1e-4, 1e-8])
+def test_exact_sum_scale_follows_the_state(variant, dims, shape, bc, factor):
+    """The exact-sum stencil takes its fixed-point scale from the state before
+    every step: a state written into psi after creation at 1e2, 1e-4 or 1e-8
+    times the one the context was created with integrates to the FP64 bar."""
+    psi, V = problem(shape, 91, bc=bc)
+    h, a, s, order = 0.3, 0.6, -1.0, 4
+    x = factor * psi
+    dt = 0.2 * O.stability_bound(dims, h, a, order, float(np.max(V)), abs(s) * 1.7 * max(1.0, factor) ** 2)
+    g = Integrator(psi, h, a, s, V, bc, order, "c128")
+    g.set_kernel(variant)
+    g.psi.copy_(torch.from_numpy(x).to(g.psi.device))
+    g.step(21, dt)
+    compare(g.numpy(), O.rk4(x, h, a, s, dt, 21, V, BCS[bc], order), "c128")
+
+
+@pytest.mark.parametrize("bc", ["dirichlet", "l0", "periodic"])
 @pytest.mark.parametrize("variant", [2, 3])
 @pytest.mark.parametrize("dims,shape", [(2, (19, 45)), (3, (9, 21, 70))])
 def test_exact_sum_out_of_range_falls_back(variant, dims, shape, bc):
-    """The exact-sum stencil fixes its range from Psi at creation; a state
-    scaled far beyond it afterwards must still integrate correctly (every
-    out-of-range site takes the FP64 stencil)."""
-    psi, V = problem(shape, 91)
+    """With the fixed-point range made 2^12 too small for the state (test
+    hook), every site's stencil operands are out of range and every site
+    takes the FP64 stencil: the result still meets the FP64 bar."""
+    psi, V = problem(shape, 91, bc=bc)
     h, a, s, order = 0.3, 0.6, -1.0, 4
-    big = 100.0 * psi
-    dt = 0.2 * O.stability_bound(dims, h, a, order, float(np.max(V)), abs(s) * 1.7e4)
+    dt = 0.2 * O.stability_bound(dims, h, a, order, float(np.max(V)), abs(s) * 1.7)
     g = Integrator(psi, h, a, s, V, bc, order, "c128")
     g.set_kernel(variant)
-    g.psi.copy_(torch.from_numpy(big).to(g.psi.device))
+    g.debug_set(L.DEBUG_FIX_OFFSET, 12)
     g.step(4, dt)
-    ref = O.rk4(big, h, a, s, dt, 4, V, BCS[bc], order)
-    compare(g.numpy(), ref, "c128")
+    compare(g.numpy(), O.rk4(psi, h, a, s, dt, 4, V, BCS[bc], order), "c128")
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64", "c64_acc64"])
+def test_refresh_potential_takes_new_values(dtype):
+    """V written after creation takes effect after nlse_refresh_potential, in
+    every dtype alike (the FP64 stages' scaled copy and max|V| are re-read)."""
+    shape = (9, 21, 70)
+    psi, V = problem(shape, 41)
+    V2 = 2.0 * V + 0.1
+    h, a, s, order = 0.3, 0.6, -1.0, 4
+    dt = stable_dt(shape, h, a, s, order, V2)
+    g = Integrator(psi, h, a, s, V, "msd", order, dtype)
+    g.V.copy_(torch.from_numpy(V2).to(g.V.dtype).to(g.V.device))
+    between = 0.5 * (O.stability_bound(3, h, a, order, float(np.max(V)), 0.0) +
+                     O.stability_bound(3, h, a, order, float(np.max(V2)), 0.0))
+    g.step(0, between)                       # within the bound of the potential the context read at creation
+    g.refresh_potential()
+    with pytest.raises(L.NLSEError) as e:    # above the bound of the new potential
+        g.step(1, between)
+    assert e.value.code == L.NLSE_EUNSTABLE
+    g.step(17, dt)
+    Vh = V2.astype(np.float32).astype(np.float64) if dtype != "c128" else V2
+    compare(g.numpy(), O.rk4(psi, h, a, s, dt, 17, Vh, W.BC_MSD, order), dtype)
 
 
 @pytest.mark.parametrize("dtype", ["c128", "c64"])
