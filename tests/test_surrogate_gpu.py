@@ -51,31 +51,51 @@ def test_forward_matches_reference(shape, tc):
     out = sur.forward(x).cpu().numpy()
     dy_ref, dy = ref - psi, out - psi
     assert np.linalg.norm(dy - dy_ref) <= 2e-2 * np.linalg.norm(dy_ref)
-    # mass projection: each state carries its input's mass
-    outp = sur.forward(x, project=True).cpu().numpy().astype(np.complex128)
+    # mass projection: each state carries its input's mass; the masses reported are the input's and
+    # the raw output's (before the projection)
+    masses = torch.zeros((x.shape[0], 2), dtype=torch.float64, device=x.device)
+    outp = sur.forward(x, project=True, masses=masses).cpu().numpy().astype(np.complex128)
     refp = S.project_mass(psi, out.astype(np.complex128))
     assert np.max(np.abs(outp - refp)) <= 1e-6 * np.max(np.abs(refp))
     m_in = np.sum(np.abs(psi) ** 2, axis=(1, 2))
     m_out = np.sum(np.abs(outp) ** 2, axis=(1, 2))
     assert np.all(np.abs(m_out - m_in) <= 1e-6 * m_in)
+    m = masses.cpu().numpy()
+    assert np.allclose(m[:, 0], m_in, rtol=1e-12)
+    assert np.allclose(m[:, 1], np.sum(np.abs(out.astype(np.complex128)) ** 2, axis=(1, 2)), rtol=1e-12)
 
 
 def test_forward_rejects_bad_batches():
     sur, psi, target, C, L, dil = small_net()
     x = torch.as_tensor(psi, dtype=torch.complex64).cuda()
     with pytest.raises(L_.NLSEError) as e:
-        L_.check(sur.lib.nlse_sur_forward(sur.s, sur.max_batch + 1, x.data_ptr(), x.data_ptr(), 0))
+        L_.check(sur.lib.nlse_sur_forward(sur.s, sur.max_batch + 1, x.data_ptr(), x.data_ptr(), 0, None))
     assert e.value.code == L_.NLSE_EINVAL
     with pytest.raises(ValueError):
         sur.gradients(x, x[:1])
+    with pytest.raises(L_.NLSEError):
+        sur.set_mass_weight(-1.0)
 
 
+def test_compare_is_the_relative_l2_per_state():
+    sur, psi, target, C, L, dil = small_net(nb=2)
+    a = torch.as_tensor(psi, dtype=torch.complex64).cuda()
+    b = torch.as_tensor(target, dtype=torch.complex64).cuda()
+    got = sur.compare(a, b)
+    an, bn = a.cpu().numpy().astype(np.complex128), b.cpu().numpy().astype(np.complex128)
+    ref = np.linalg.norm((an - bn).reshape(2, -1), axis=1) / np.linalg.norm(bn.reshape(2, -1), axis=1)
+    assert np.allclose(got, ref, rtol=1e-12)
+
+
+@pytest.mark.parametrize("mass_weight", [0.0, 0.5])
 @pytest.mark.parametrize("shape,tc", SHAPES, ids=IDS)
-def test_gradients_match_reference(shape, tc):
-    """BF16 operands, FP32 accumulation: the gradient vector within 3 % (relative L2)."""
+def test_gradients_match_reference(shape, tc, mass_weight):
+    """BF16 operands, FP32 accumulation: the gradient vector within 3 % (relative L2),
+    with and without the loss's mass term."""
     sur, psi, target, C, L, dil = make(shape, tc)
+    sur.set_mass_weight(mass_weight)
     params = bf16_round(sur.params.cpu().numpy())
-    loss_ref, g_ref = S.loss_and_grad(params, psi, target, C, L, dil)
+    loss_ref, g_ref = S.loss_and_grad(params, psi, target, C, L, dil, mass_weight)
     x = torch.as_tensor(psi, dtype=torch.complex64).cuda()
     t = torch.as_tensor(target, dtype=torch.complex64).cuda()
     g, loss = sur.gradients(x, t)
@@ -124,21 +144,43 @@ def test_noisy_training_is_seeded_and_learns():
 
 
 def test_fallback_takes_over_from_a_bad_network():
-    """A network that is far off (large random weights, no mass projection) is
-    rejected on every window, so the rollout equals plain RK4 (up to the
-    complex64 hand-over between windows)."""
+    """A network that is far off (large random weights) is rejected on every
+    window, with or without the mass projection (the mass is judged on its
+    raw output), so the rollout equals plain RK4 (up to the complex64
+    hand-over between windows)."""
     n, windows = 48, 6
     psi0 = W.humps_2d(5, 0, n=n, h=FOCUSING["h"])
-    sur = Surrogate(n, n, channels=16, layers=4, dilations=(1, 2, 2, 1), max_batch=1, seed=3)
+    sur = Surrogate(n, n, channels=16, layers=4, dilations=(1, 2, 2, 1), max_batch=4, seed=3)
     sur.load_params(sur.params * 40.0)
     ref, _ = rollout(None, psi0, windows)
     for mode, project in (("strict", False), ("sampled", False), ("strict", True), ("parallel", True)):
         got, st = rollout(sur, psi0, windows, mode=mode, every=3, project=project, width=4)
         assert st.accepted == 0 and st.rk4_windows == windows
         assert st.rejected_l2 + st.rejected_mass >= 1
-        if project and mode == "strict":
-            assert st.rejected_l2 == windows and st.rejected_mass == 0
+        if mode == "strict":
+            assert st.rejected_mass == windows and st.rejected_l2 == 0
         assert float(torch.linalg.vector_norm(got - ref) / torch.linalg.vector_norm(ref)) <= 1e-5
+
+
+@pytest.mark.parametrize("mode", ["strict", "sampled", "parallel"])
+def test_mass_check_fires_with_projection_on(mode):
+    """A network whose only output is a constant shift of 1e-3 on the real
+    part, on a real Gaussian state (48 x 48, h = 0.2, width 1.5): the shift is
+    within the relative-L2 tolerance of RK4 (~4e-3), but its raw output adds
+    ~4e-3 of the mass.  With the mass projection on (the default) every window
+    must still be rejected for mass, and the rollout equals plain RK4."""
+    n, windows = 48, 6
+    psi0, _ = W.gaussian_packet_2d(n, FOCUSING["h"], 1.0, 1.5, (0.0, 0.0), (0.0, 0.0), 1.0, 1.0)
+    sur = Surrogate(n, n, channels=16, layers=4, dilations=(1, 2, 2, 1), max_batch=4, seed=3)
+    p = torch.zeros_like(sur.params)
+    p[-2] = 1e-3
+    sur.load_params(p)
+    ref, _ = rollout(None, psi0, windows)
+    got, st = rollout(sur, psi0, windows, mode=mode, every=3, project=True, width=4)
+    assert st.accepted == 0 and st.rk4_windows == windows
+    assert st.rejected_mass >= 1 and st.rejected_l2 == 0
+    assert st.max_mass_drift > 1e-3
+    assert float(torch.linalg.vector_norm(got - ref) / torch.linalg.vector_norm(ref)) <= 1e-5
 
 
 def test_gain_over_plain_rk4():
