@@ -60,14 +60,39 @@ FP64_FLOPS_PER_SITE_STEP = 15 + 19 + 19 + 17
 CHUNK = 56   # steps per frame in the end-to-end measurement (the 87x87x203 run's chunk size)
 
 
-# DRAM bytes (read + write) per RK4 step of the stage kernels on this workload,
-# from one ncu capture (profiles/), or None when the kernels changed since.
-LAUNCHES_PER_STEP = 16   # 3D, every extent >= 7 (x >= 10): per stage 1 deep-interior + 3 wall-slab kernels
-TRAFFIC_PER_STEP = {  # one ncu capture of trap_vortex_3d_256x256x512, current kernels
-    "c128": 10819.8e6,
-    "c64": 5461.3e6,
-    "c64_acc64": 6230.8e6,
+# Kernel launches per RK4 step of the 3D tiled path (every extent >= 7, x >= 10): per stage one
+# deep-interior kernel and three wall-slab kernels; the FP64 exact-sum form adds the one-thread kernel
+# that sets the next step's fixed-point scale.
+LAUNCHES_PER_STEP = {"c128": 17, "c64": 16, "c64_acc64": 16}
+
+# DRAM bytes (read + write) per RK4 step of the stage kernels on trap_vortex_3d_256x256x512, from one
+# ncu capture (profiles/rk4_step_256x256x512_traffic_and_launches.md), with the hash of the kernel
+# sources it was taken at: the figure is reported only while csrc_hash() still matches.
+TRAFFIC_PER_STEP = {  # dtype -> (bytes per step, csrc hash of the capture)
+    "c128": (10819.8e6, None),
+    "c64": (5461.3e6, None),
+    "c64_acc64": (6230.8e6, None),
 }
+
+
+def csrc_hash():
+    """sha256 (first 16 hex digits) over the CUDA sources and headers the kernels are built from."""
+    import glob
+    import hashlib
+    h = hashlib.sha256()
+    for f in sorted(glob.glob(os.path.join(ROOT, "paper_1203_1263_gb300", "csrc", "*")) +
+                    glob.glob(os.path.join(ROOT, "include", "*.h"))):
+        h.update(os.path.basename(f).encode())
+        h.update(open(f, "rb").read())
+    return h.hexdigest()[:16]
+
+
+def traffic_for(dtype, workload):
+    """ncu bytes per step for the current kernels, or None (other workload, or kernels changed since)."""
+    if workload != "trap_vortex_3d_256x256x512" or dtype not in TRAFFIC_PER_STEP:
+        return None
+    nbytes, at = TRAFFIC_PER_STEP[dtype]
+    return nbytes if at is not None and at == csrc_hash() else None
 
 
 def peaks():
@@ -93,20 +118,22 @@ FP64_PEAK_TFLOPS_MEASURED = 0.998
 
 
 def roofline_for(dtype, sites, step_s, with_v):
-    """The roofline that binds each form: FP64 is bound by the FP64 pipe, the
-    FP32 forms by HBM."""
+    """HBM roofline of one RK4 step on the stage-streaming bytes (304 B per site with V for FP64, 152 B
+    for FP32, 176 B for FP32 stages with the FP64 master), and, for FP64, the FP64-pipe view (the pipe
+    that binds that form on GB300) as a second figure."""
     hbm_peak, kind = peaks()
     bytes_site = ALG_BYTES[dtype][0 if with_v else 1]
     gbs = sites * bytes_site / step_s / 1e9
     hbm = {"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm_peak, "unit": "GB/s",
-           "frac": round(gbs / hbm_peak, 4), "peak_kind": kind, "alg_bytes_per_site_step": bytes_site}
-    if dtype != "c128":
-        return hbm, None
-    tflops = sites * FP64_FLOPS_PER_SITE_STEP / step_s / 1e12
-    alu = {"bound": "alu", "achieved": round(tflops, 4), "peak": FP64_PEAK_TFLOPS_MEASURED, "unit": "TFLOP/s",
-           "frac": round(tflops / FP64_PEAK_TFLOPS_MEASURED, 4), "peak_kind": "measured (FP64 FMA probe)",
-           "alg_flops_per_site_step": FP64_FLOPS_PER_SITE_STEP}
-    return alu, hbm
+           "frac": round(gbs / hbm_peak, 4), "peak_kind": kind + " (MEASURED_PEAKS.json copy bandwidth)",
+           "alg_bytes_per_site_step": bytes_site}
+    if dtype == "c128":
+        tflops = sites * FP64_FLOPS_PER_SITE_STEP / step_s / 1e12
+        hbm["fp64_pipe_view"] = {"achieved": round(tflops, 4), "peak": FP64_PEAK_TFLOPS_MEASURED, "unit": "TFLOP/s",
+                                 "frac": round(tflops / FP64_PEAK_TFLOPS_MEASURED, 4),
+                                 "peak_kind": "measured with an FP64 FMA probe on this pool's GB300s",
+                                 "flops_per_site_step": FP64_FLOPS_PER_SITE_STEP}
+    return hbm
 
 
 # ---------------------------------------------------------------------------
@@ -182,6 +209,16 @@ def job_throughput(site_steps_per_rank, seconds, device, world=1, dist=None):
     return world * site_steps_per_rank / slowest_rank(seconds, device, dist) / 1e9
 
 
+def workload_config(p, dt, precision, world, workload):
+    """The `config` object of the JSON line (the same for both arms)."""
+    big = p.sites * 16 > 129e6
+    return {"workload": workload, "grid": list(p.shape), "h": p.h, "a": p.a, "s": p.s, "order": p.order,
+            "bc": "msd", "dt": dt, "precision": precision,
+            "l2": ("inputs larger than L2 (%.0f MB per state array)" % (p.sites * 16 / 1e6)) if big else
+                  "state fits in L2",
+            "parallelism": "replicas" if world > 1 else "single"}
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     from paper_1203_1263_gb300.integrator import Integrator, max_dt
@@ -204,88 +241,122 @@ def run_ours(args, rank, world, local_rank):
     sites = p.sites
     stream = torch.cuda.Stream(dev)
 
-    def timed(dtype, K, Wm, bc="msd"):
+    def timed(dtype, K, Wm, bc="msd", prob=None, dt_=None, repeats=1, sample_clocks=False):
+        """K steps timed with CUDA events on the integrator's stream, `repeats` times; returns the
+        integrator, the milliseconds of each repeat and the clock record."""
+        prob = p if prob is None else prob
+        dt_ = dt if dt_ is None else dt_
         with torch.cuda.stream(stream):
-            g = Integrator(p.psi0, p.h, p.a, p.s, p.V, bc, p.order, dtype, device=dev, stream=stream)
+            g = Integrator(prob.psi0, prob.h, prob.a, prob.s, prob.V, bc, prob.order, dtype, device=dev, stream=stream)
             if args.variant is not None or args.tile != -1:
                 g.set_kernel(args.variant if args.variant is not None else (2 if dtype == "c128" else 1), args.tile)
-            g.step(Wm, dt)
+            g.step(Wm, dt_)
             g.sync()
             barrier()
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            clk = ClockSampler(local_rank)
-            clk.start()
-            w0 = time.perf_counter()
-            e0.record(stream)
-            g.step(K, dt)
-            e1.record(stream)
-            e1.synchronize()
-            wall = time.perf_counter() - w0
-            clocks = clk.stop()
-            ms = e0.elapsed_time(e1)
+            clk = ClockSampler(local_rank) if sample_clocks else None
+            if clk:
+                clk.start()
+            ms = []
+            for _ in range(repeats):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                g.step(K, dt_)
+                e1.record(stream)
+                e1.synchronize()
+                ms.append(e0.elapsed_time(e1))
+            clocks = clk.stop() if clk else None
             g.sync()
             barrier()
-        return g, ms, wall, clocks
+        return g, ms, clocks
 
     K, Wm = args.steps, args.warmup
-    g64, ms, wall, clocks = timed(args.dtype, K, Wm)
-    ms_max = slowest_rank(ms, dev, dist)
+    # the timed region of the contract is the first repeat; the others give the median of the spread
+    g64, ms_all, clocks = timed(args.dtype, K, Wm, repeats=max(1, args.repeats), sample_clocks=True)
+    ms_max = slowest_rank(ms_all[0], dev, dist)
     value = world * sites * K / (ms_max * 1e-3) / 1e9
 
-    result = None
+    result, details, forms = None, {}, {}
     if rank == 0:
         step_s = ms_max * 1e-3 / K
-        roof, hbm_view = roofline_for(args.dtype, sites, step_s, p.V is not None)
-        roof["traffic"] = TRAFFIC_PER_STEP.get(args.dtype) if args.workload == "trap_vortex_3d_256x256x512" else None
+        roof = roofline_for(args.dtype, sites, step_s, p.V is not None)
+        roof["traffic"] = traffic_for(args.dtype, args.workload)
         roof["traffic_unit"] = "bytes per RK4 step (ncu dram__bytes_read.sum + dram__bytes_write.sum)"
         roof["kernel"] = ("one RK4 step: 4 fused stage kernels (deep interior, TMA-fed) + 12 wall-slab kernels "
                           "(3 per stage, shared-memory staged)")
+        med = statistics.median(ms_all) / K
         result = {
             "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world, "steps": K, "warmup": Wm,
             "ms_per_step": round(ms_max / K, 4), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": {"c128": "f64", "c64": "f32", "c64_acc64": "f32+f64acc"}[args.dtype],
             "data": "synthetic (seeded trap-vortex IC, no dataset)",
-            "config": {"workload": args.workload, "grid": list(p.shape), "h": p.h, "a": p.a, "s": p.s,
-                       "order": p.order, "bc": "msd", "dt": dt, "precision": args.dtype,
-                       "l2": "inputs larger than L2 (%.0f MB per state array)" % (sites * 16 / 1e6),
-                       "parallelism": "replicas" if world > 1 else "single"},
-            "roofline": roof, "clocks": clocks, "gpu_launches": LAUNCHES_PER_STEP * K,
+            "config": workload_config(p, dt, args.dtype, world, args.workload),
+            "roofline": roof, "clocks": clocks, "gpu_launches": LAUNCHES_PER_STEP[args.dtype] * K,
+            "timing": {"repeats": len(ms_all), "ms_per_step": [round(m / K, 4) for m in ms_all],
+                       "median_ms_per_step": round(med, 4),
+                       "median_value": round(sites / (med * 1e-3) / 1e9, 4)},
         }
-        if hbm_view is not None:
-            result["hbm_roofline"] = hbm_view
 
-    # ---- other precision forms on the same problem (speed-up over FP64 at a stated accuracy) ----
+    # ---- other precision forms and boundaries on the same problem (speed-up over FP64 at a stated accuracy) ----
     if not args.no_forms and rank == 0:
         ref_state = g64.numpy()
-        forms = {}
         for dt_name in ("c64", "c64_acc64"):
             if dt_name == args.dtype:
                 continue
-            g2, ms2, _, _ = timed(dt_name, K, Wm)
+            g2, ms2, _ = timed(dt_name, K, Wm)
             st = g2.numpy().astype(np.complex128)
             rl2 = float(np.linalg.norm((st - ref_state).ravel()) / np.linalg.norm(ref_state.ravel()))
-            v2 = sites * K / (ms2 * 1e-3) / 1e9
-            r2, _ = roofline_for(dt_name, sites, ms2 * 1e-3 / K, p.V is not None)
-            r2["traffic"] = TRAFFIC_PER_STEP.get(dt_name) if args.workload == "trap_vortex_3d_256x256x512" else None
-            forms[dt_name] = {"value": round(v2, 4), "unit": UNIT, "speedup_vs_f64": round(v2 / value, 3),
-                              "rel_l2_vs_f64_gpu": rl2, "roofline": r2}
+            v2 = sites * K / (ms2[0] * 1e-3) / 1e9
+            r2 = roofline_for(dt_name, sites, ms2[0] * 1e-3 / K, p.V is not None)
+            r2["traffic"] = traffic_for(dt_name, args.workload)
+            details[dt_name] = {"value": round(v2, 4), "unit": UNIT, "speedup_vs_f64": round(v2 / value, 3),
+                                "rel_l2_vs_f64_gpu_after_warmup_plus_steps": rl2, "roofline": r2}
+            forms[dt_name] = {"value": round(v2, 3), "x_f64": round(v2 / value, 3), "hbm_frac": r2["frac"],
+                              "rel_l2_vs_f64": float("%.2e" % rl2)}
             g2.close()
-        # the Laplacian-zero boundary (Eqs. BCL0dt, BCL0lap) on the same grid: only the wall kernels differ
-        for dt_name in ("c128", "c64"):
-            g3, ms3, _, _ = timed(dt_name, K, Wm, "l0")
-            v3 = sites * K / (ms3 * 1e-3) / 1e9
-            r3, _ = roofline_for(dt_name, sites, ms3 * 1e-3 / K, p.V is not None)
-            r3["traffic"] = None
-            forms[dt_name + "_l0"] = {"value": round(v3, 4), "unit": UNIT, "bc": "l0", "roofline": r3}
-            g3.close()
-        result["forms"] = forms
+        # the Laplacian-zero and periodic boundaries on the same grid: only the shell kernels differ
+        for bc in ("l0", "periodic"):
+            for dt_name in ("c128", "c64"):
+                g3, ms3, _ = timed(dt_name, K, Wm, bc)
+                v3 = sites * K / (ms3[0] * 1e-3) / 1e9
+                r3 = roofline_for(dt_name, sites, ms3[0] * 1e-3 / K, p.V is not None)
+                r3["traffic"] = None
+                details[f"{dt_name}_{bc}"] = {"value": round(v3, 4), "unit": UNIT, "bc": bc, "roofline": r3}
+                forms[f"{dt_name}_{bc}"] = {"value": round(v3, 3), "hbm_frac": r3["frac"]}
+                g3.close()
+        # the paper's headline grid (87 x 87 x 203; the state fits in L2) and the precision form's 512^3 grid
+        p87 = W.trap_vortex_3d(shape=(203, 87, 87))
+        dt87 = 0.8 * max_dt(3, p87.h, p87.a, 4, p87.vmax(), abs(p87.s) * float(np.max(np.abs(p87.psi0))) ** 2)
+        for dt_name in ("c128", "c64_acc64"):
+            g4, ms4, _ = timed(dt_name, 4 * K, Wm, prob=p87, dt_=dt87)
+            v4 = p87.sites * 4 * K / (ms4[0] * 1e-3) / 1e9
+            details[f"trap_87x87x203_{dt_name}"] = {"value": round(v4, 4), "unit": UNIT, "steps": 4 * K,
+                                                    "ms_per_step": round(ms4[0] / (4 * K), 4)}
+            forms[f"trap87_{dt_name}"] = {"value": round(v4, 3)}
+            g4.close()
+        del p87
+        if args.rings:
+            details["rings_512cube"] = rings_form(args, dev, timed, K, Wm)
+            forms["rings512"] = {k: details["rings_512cube"][k] for k in ("c128", "c64_acc64", "x_f64",
+                                                                         "rel_l2_after_steps")}
+        details["soliton_1d_2001"] = soliton_form(dev)
+        forms["soliton1d"] = {k: details["soliton_1d_2001"][k]["us_per_step"] for k in ("c128", "c64")}
 
     if not args.no_batch and rank == 0:
-        result.setdefault("forms", {})["batch"] = batch_form(args, dev, min(K, 200), Wm)
+        details["batch"] = batch_form(args, dev, min(K, 200), Wm)
+        b = details["batch"]
+        forms["batch"] = {"value": round(b["value"], 3), "x_f64": b["speedup_vs_f64"], "hbm_frac": b["roofline"]["frac"],
+                          "rel_l2_vs_f64": float("%.2e" % b["max_rel_l2_vs_f64_gpu"])}
 
     if not args.no_surrogate and rank == 0:
-        result.setdefault("forms", {})["surrogate"] = surrogate_form(args, dev)
+        details["surrogate"] = surrogate_form(args, dev)
+        su = details["surrogate"]
+        forms["surrogate"] = {"train_tflops": su.get("train_tflops"), "bf16_frac": su["roofline"]["frac"]}
+        if "rollout_t20" in su:
+            sm = su["rollout_t20"]["summary"]
+            forms["surrogate"].update({m: {"x_f64": sm[m]["mean_speedup_vs_f64"], "accepted": sm[m]["accepted_windows"],
+                                           "final_rel_l2": float("%.2e" % sm[m]["max_final_rel_l2_vs_plain_f64"])}
+                                       for m in ("parallel", "sampled")})
 
     if not args.no_paper_tables and rank == 0:
         result["paper_tables"] = paper_tables(dev)
@@ -325,10 +396,78 @@ def run_ours(args, rank, world, local_rank):
     # ---- CPU baseline: the oracle on a bounded sample of the same workload ----
     if rank == 0 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline(p, dt, budget_s=args.cpu_budget)
+    if rank == 0:
+        if details:
+            result["details"] = details
+        if forms:      # last, so that the summary of every form is in the tail of the line
+            result["forms"] = forms
     if dist is not None:
         dist.barrier()
         dist.destroy_process_group()
     return result
+
+
+def rings_form(args, dev, timed, K, Wm):
+    """The precision form's workload: 512^3 vortex rings (h = 0.25, V = 0, MSD, 2SHOC), FP64 against FP32
+    stages with the FP64 master and accumulator, K steps each, and their relative L2 after them."""
+    pr = W.vortex_rings_3d(n=512)
+    dtr = 0.8 * nlse_bound(pr)
+    out = {"grid": list(pr.shape), "dt": dtr, "steps": K}
+    states = {}
+    for dt_name in ("c128", "c64_acc64"):
+        g, ms, _ = timed(dt_name, K, Wm, prob=pr, dt_=dtr)
+        v = pr.sites * K / (ms[0] * 1e-3) / 1e9
+        r = roofline_for(dt_name, pr.sites, ms[0] * 1e-3 / K, False)
+        out[dt_name] = round(v, 3)
+        out[dt_name + "_roofline"] = r
+        states[dt_name] = g.numpy()
+        g.close()
+    a, b = states["c128"], states["c64_acc64"]
+    out["rel_l2_after_steps"] = float("%.2e" % (np.linalg.norm((b - a).ravel()) / np.linalg.norm(a.ravel())))
+    out["x_f64"] = round(out["c64_acc64"] / out["c128"], 3)
+    out["warmup_plus_steps"] = Wm + K
+    return out
+
+
+def nlse_bound(p):
+    from paper_1203_1263_gb300.integrator import max_dt
+    return max_dt(p.dims, p.h, p.a, p.order, p.vmax(), abs(p.s) * float(np.max(np.abs(p.psi0))) ** 2)
+
+
+def soliton_form(dev, steps=32000):
+    """The 1D bright soliton (N = 2001, h = 0.05, dt = h^2/8, Dirichlet, 2SHOC) over its 32,000 steps to
+    t = 10 through one nlse_step call (CUDA events), FP64 and FP32: the line runs on one thread-block
+    cluster; a tenth of the steps on the per-site kernel for comparison."""
+    import torch
+    from paper_1203_1263_gb300.integrator import Integrator
+    p = W.bright_soliton_1d(order=4)
+    out = {"grid": list(p.shape), "dt": p.dt, "steps": steps}
+    stream = torch.cuda.Stream(dev)
+    for dt_name, per_site in (("c128", 3), ("c64", 0)):
+        row = {}
+        for variant, n in ((None, steps), (per_site, steps // 10)):
+            with torch.cuda.stream(stream):
+                g = Integrator(p.psi0, p.h, p.a, p.s, None, "dirichlet", 4, dt_name, device=dev, stream=stream)
+                if variant is not None:
+                    g.set_kernel(variant)
+                g.step(64, p.dt)
+                g.sync()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                g.step(n, p.dt)
+                e1.record(stream)
+                e1.synchronize()
+                ms = e0.elapsed_time(e1)
+                key = "default" if variant is None else "per_site_kernel"
+                row[key] = {"kernel": g.kernel_in_use(), "value": round(p.sites * n / (ms * 1e-3) / 1e9, 4),
+                            "unit": UNIT, "us_per_step": round(ms * 1e3 / n, 3)}
+                g.close()
+        row["us_per_step"] = row["default"]["us_per_step"]
+        row["seconds_for_32000_steps"] = round(row["default"]["us_per_step"] * 32000 / 1e6, 4)
+        row["x_per_site_kernel"] = round(row["per_site_kernel"]["us_per_step"] / row["default"]["us_per_step"], 2)
+        out[dt_name] = row
+    return out
 
 
 # The paper's GPU times (seconds) for its timing workloads, 10,000 steps, chunk
@@ -461,32 +600,48 @@ def batch_form(args, dev, K, Wm):
             "f64_sequential": round(v64, 4), "f32_sequential": round(v32, 4),
             "speedup_vs_f32_sequential": round(v_batch / v32, 3),
             "max_rel_l2_vs_f64_gpu": max(errs), "dtype": "f32",
-            "roofline": roofline_for("c64", sites, t_batch / K, True)[0]}
+            "roofline": roofline_for("c64", sites, t_batch / K, True)}
 
 
-def cpu_baseline(p, dt, budget_s=20.0, steps=None):
-    """The oracle as it stands, on all host cores, on a z-slab of the workload."""
+def cpu_model():
+    """The host CPU's model name (lscpu), for the record next to the oracle's timings."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return platform.processor() or platform.machine()
+
+
+def oracle_rate(p, dt, threads, budget_s, nsteps=2):
+    """The oracle as it stands on `threads` host threads, on a z-slab of the workload sized to take about
+    budget_s seconds: (Gsite*step/s, threads used, sample description)."""
     import oracle
-    cores = oracle.set_threads(os.cpu_count() or 1)
-    # size the slab so that the run takes about budget_s seconds (first a probe)
-    nz_probe = min(p.shape[0], 16)
-    sl = p.psi0[:nz_probe]
-    Vs = p.V[:nz_probe] if p.V is not None else None
+    used = oracle.set_threads(threads)
+    nz_probe = min(p.shape[0], 16 if threads > 1 else 5)
+    sl = np.ascontiguousarray(p.psi0[:nz_probe])
+    Vs = np.ascontiguousarray(p.V[:nz_probe]) if p.V is not None else None
     t0 = time.perf_counter()
     oracle.rk4(sl, p.h, p.a, p.s, dt, 1, Vs, p.bc, p.order)
-    t_probe = time.perf_counter() - t0
-    per_site = t_probe / sl.size
-    nsteps = steps or 2
+    per_site = (time.perf_counter() - t0) / sl.size
     nz = int(max(5, min(p.shape[0], budget_s / (per_site * nsteps * sl[0].size))))
     sl = np.ascontiguousarray(p.psi0[:nz])
     Vs = np.ascontiguousarray(p.V[:nz]) if p.V is not None else None
     t0 = time.perf_counter()
     oracle.rk4(sl, p.h, p.a, p.s, dt, nsteps, Vs, p.bc, p.order)
     el = time.perf_counter() - t0
-    v = sl.size * nsteps / el / 1e9
-    return {"value": round(v, 6), "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{nsteps} RK4 steps on a {nz}x{p.shape[1]}x{p.shape[2]} slab of the workload "
-                      f"({el:.1f} s, FP64, {platform.machine()})"}
+    return sl.size * nsteps / el / 1e9, used, (f"{nsteps} RK4 steps on a {nz}x{p.shape[1]}x{p.shape[2]} slab of the "
+                                               f"workload ({el:.1f} s, FP64, {platform.machine()})")
+
+
+def cpu_baseline(p, dt, budget_s=20.0):
+    """The oracle as it stands on all host cores (the value) and on one core (the paper's serial baseline)."""
+    v, cores, sample = oracle_rate(p, dt, os.cpu_count() or 1, budget_s)
+    v1, _, sample1 = oracle_rate(p, dt, 1, budget_s / 2)
+    return {"value": round(v, 6), "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
+            "cpu_model": cpu_model(), "serial": {"value": round(v1, 6), "unit": UNIT, "cores": 1, "sample": sample1}}
 
 
 # ---------------------------------------------------------------------------
@@ -520,10 +675,9 @@ def run_reference(args, rank, world):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(el / args.steps * 1e3, 3),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded trap-vortex IC, no dataset)",
-            "config": {"workload": args.workload, "grid": list(p.shape), "order": p.order, "bc": "msd",
-                       "dt": dt, "precision": "c128"},
+            "config": workload_config(p, dt, "c128", world, args.workload),
             "cpu_baseline": {"value": round(v, 6), "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": sample},
+                             "sample": sample, "cpu_model": cpu_model()},
             "e2e": {"value": round(v, 6), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
@@ -600,7 +754,8 @@ def surrogate_form(args, dev):
     t_gen = time.perf_counter() - t0
     sur = Surrogate(n, n, channels=C, layers=nl, dilations=dil, max_batch=32, seed=7)
     t0 = time.perf_counter()
-    hist = train(sur, X, Y, epochs=args.sur_epochs, batch=32, lr=5e-4, lr_end=1e-5, seed=0, noise=3e-3)
+    hist = train(sur, X, Y, epochs=args.sur_epochs, batch=32, lr=5e-4, lr_end=1e-5, seed=0, noise=3e-3,
+                 mass_weight=args.sur_mass_weight)
     torch.cuda.synchronize(dev)
     t_train_run = time.perf_counter() - t0
     del X, Y
@@ -612,7 +767,7 @@ def surrogate_form(args, dev):
         if len(held) == 3:
             break
     out["training"] = {"pairs": int(kept * 125), "trajectories": kept, "epochs": args.sur_epochs, "batch": 32,
-                       "lr": "cosine 5e-4 -> 1e-5", "input_noise": 3e-3,
+                       "lr": "cosine 5e-4 -> 1e-5", "input_noise": 3e-3, "mass_weight": args.sur_mass_weight,
                        "loss_first_epoch": hist[0], "loss_last_epoch": hist[-1],
                        "data_seconds": round(t_gen, 2), "train_seconds": round(t_train_run, 2)}
     psi_w = held[0][1]
@@ -625,12 +780,12 @@ def surrogate_form(args, dev):
         rolls = {"seed": seed, "plain_f64_seconds": round(st_plain.seconds, 4)}
         for mode in ("strict", "sampled", "parallel"):
             got, st = rollout(sur, psi0, 125, mode=mode, every=4, width=8)
-            err = float(torch.linalg.vector_norm(got - ref) / torch.linalg.vector_norm(ref))
+            err = float(sur.compare(got[None], ref[None])[0])
             rolls[mode] = {"seconds": round(st.seconds, 4),
                            "speedup_vs_f64": round(st_plain.seconds / st.seconds, 3),
                            "accepted_windows": st.accepted, "rk4_windows": st.rk4_windows, "checked": st.checked,
                            "rejected_l2": st.rejected_l2, "rejected_mass": st.rejected_mass,
-                           "max_mass_drift_per_window": st.max_mass_drift,
+                           "max_raw_mass_drift_vs_m0": st.max_mass_drift,
                            "median_check_rel_l2": float(np.median(st.l2_errors)) if st.l2_errors else None,
                            "final_rel_l2_vs_plain_f64": err}
         per_state.append(rolls)
@@ -639,7 +794,7 @@ def surrogate_form(args, dev):
                    "max_final_rel_l2_vs_plain_f64": max(r[m]["final_rel_l2_vs_plain_f64"] for r in per_state)}
                for m in ("strict", "sampled", "parallel")}
     out["rollout_t20"] = {"windows": 125, "every": 4, "parallel_width": 8,
-                          "tolerances": {"rel_l2": 1e-2, "mass_drift": 1e-4},
+                          "tolerances": {"rel_l2": 1e-2, "mass_drift_of_raw_output_vs_m0": 1e-4},
                           "summary": summary, "held_out": per_state}
     sur.close()
     return out
@@ -669,6 +824,11 @@ def main():
     ap.add_argument("--no-paper-tables", action="store_true", help="skip the timing runs of the paper's Tables 1-3")
     ap.add_argument("--chunk-study", action="store_true", help="also time 1000 steps in chunks of 1..1000")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--repeats", type=int, default=5, help="timed repeats of K steps (the first is the value)")
+    ap.add_argument("--no-rings", dest="rings", action="store_false",
+                    help="skip the 512^3 precision-form leg")
+    ap.add_argument("--sur-mass-weight", type=float, default=10.0,
+                    help="weight of the mass-conservation term of the surrogate's training loss")
     ap.add_argument("--ref-budget", type=float, default=90.0)
     args = ap.parse_args()
     if args.warmup < 3:

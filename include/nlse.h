@@ -161,8 +161,11 @@ const char *nlse_last_error(void);
 
 /* Which stage kernel the context uses:
  *   0 = generic one-thread-per-site kernel,
- *   1 = tiled kernel (2D halo tiles / 3D z-marching; 1D grids always use the
- *       generic kernel),
+ *   1 = tiled kernel (2D halo tiles / 3D z-marching; on 1D lines of up to
+ *       ~49,000 sites in FP64 or ~98,000 in FP32 (not NLSE_C64_ACC64) one
+ *       thread-block cluster of up to 16 CTAs keeps the line in shared memory
+ *       and runs every step of an nlse_step call in one launch; longer lines
+ *       and the mixed form use the generic kernel),
  *   2 = tiled kernel with the exact-sum stencil (NLSE_C128 only; other
  *       dtypes treat it as 1): the Laplacian's stencil sums are formed exactly
  *       in 64-bit fixed point on the integer pipe and converted to FP64 once,

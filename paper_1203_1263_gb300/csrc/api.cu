@@ -116,6 +116,7 @@ struct nlse_ctx {
   signed char fmap_state[3];
   long long spin_limit;           // bound on device-side waits (cycles)
   unsigned int extra_tx;          // test hook, see nlse_debug_set
+  bool line_failed;               // the 1D cluster path could not be launched here: per-site kernel instead
   cudaStream_t side;              // wall-shell kernels run here, concurrently with the deep kernels
   cudaEvent_t ev_fork, ev_join;
 
@@ -307,6 +308,24 @@ LaunchCfg launch_cfg(const nlse_ctx* c) {
   L.ev_fork = c->ev_fork;
   L.ev_join = c->ev_join;
   return L;
+}
+
+// 1D lines that take the cluster path: FP64 or FP32 (not the mixed form), variant 1, 2 or 4.
+bool line_path(const nlse_ctx* c) {
+  if (c->d != 1 || c->line_failed || c->dtype == NLSE_C64_ACC64) return false;
+  if (c->variant != 1 && c->variant != 2 && c->variant != 4) return false;
+  return line_ok(int(c->n[0]), c->dtype == NLSE_C128);
+}
+
+cudaError_t launch_line(const nlse_ctx* c, int64_t nsteps, double dt) {
+  if (c->dtype == NLSE_C128) {
+    StageArgs<P64> A[4];
+    for (int s = 1; s <= 4; ++s) A[s - 1] = stage_args<P64>(c, s, dt, c->psi, c->psi);
+    return launch_line_steps<P64>(A, nsteps, int(c->n[0]), c->order, c->exact(), c->fixF, c->fix_offset, c->stream);
+  }
+  StageArgs<P32> A[4];
+  for (int s = 1; s <= 4; ++s) A[s - 1] = stage_args<P32>(c, s, dt, c->psi, c->psi);
+  return launch_line_steps<P32>(A, nsteps, int(c->n[0]), c->order, false, c->fixF, c->fix_offset, c->stream);
 }
 
 // One step of the fused path from buffer cur to buffer nxt (Psi or its ping-pong copy).
@@ -556,6 +575,7 @@ int nlse_set_kernel(nlse_t c, int variant, int tile_cfg) {
 int nlse_kernel_in_use(nlse_t c) {
   if (!c) return fail(NLSE_EINVAL, "NULL context");
   if (fused_path(c)) return 4;
+  if (line_path(c)) return c->dtype == NLSE_C128 ? 2 : 1;
   if (c->variant == 4) return c->d == 1 ? 0 : 1;
   if (c->d == 1) return (c->dtype == NLSE_C128 && c->variant >= 2) ? 3 : 0;
   if (c->dtype != NLSE_C128 && c->variant >= 2) return c->variant - 2;
@@ -595,6 +615,13 @@ int nlse_step(nlse_t c, int64_t nsteps, double dt) {
   if (e != cudaSuccess) return cuda_fail(e, "round master");
   // the exact-sum scale of the state as the caller left it (stage 4 keeps it current from here on)
   if (c->exact() && (e = update_fix(c, c->psi, c->stream)) != cudaSuccess) return cuda_fail(e, "scale");
+  if (line_path(c)) {   // 1D: the whole call on one thread-block cluster
+    e = launch_line(c, nsteps, dt);
+    if (e == cudaSuccess) return NLSE_OK;
+    if (e != cudaErrorInvalidConfiguration) return cuda_fail(e, "line launch");
+    cudaGetLastError();
+    c->line_failed = true;   // cannot be co-scheduled here: the per-site kernel from now on
+  }
   int64_t left = nsteps;
   if (nsteps >= kGraphSteps) {
     int rc = ensure_graph(c, dt);

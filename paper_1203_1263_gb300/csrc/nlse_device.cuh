@@ -110,6 +110,8 @@ struct GAcc {
   // fixed-point operands of the exact-sum stencil (FP64 fields only)
   __device__ __forceinline__ longlong2 fx0() const;
   __device__ __forceinline__ longlong2 fx1(int k, int s) const;
+  __device__ __forceinline__ longlong2 fx2(int k, int s, int j, int t) const;
+  __device__ __forceinline__ int fixF() const { return cur_fix(f); }   // this step's fraction bits
 };
 
 // h^2 D_b at the face boundary site nb = c + dir e_k (Eqs. BCDlap, BCMSDlap;
@@ -262,29 +264,54 @@ __device__ __forceinline__ double2 a_lap_slow(const Field<T>& f, const Acc& acc,
   return a_lap_body<T, D, ORDER, Acc, true>(f, acc, idx, c, pc, Nc);
 }
 
+// The ghost beyond the wall in fixed point (exact-sum stages): with fac = h^2 D_b / Psi_b (the boundary
+// Laplacian form, Eqs. BCDlap, BCMSDlap, BCL0lap) the ghost is g = 2d Psi_b + fac Psi_b - Psi_c -
+// sum_{in-face neighbours of b} Psi (see ghost()); only fac and fac Psi_b are formed in FP64, the rest of
+// the sum is exact in fixed point.  dh_c = h^2 D_c and inv_m2 = 1 / |Psi_c|^2 (0 below the MSD guard)
+// come from the caller, once per site.
+template <class T, int D, class Acc>
+__device__ __forceinline__ longlong2 ghost_fix(const Field<T>& f, const Acc& acc, int k, int dir, int64_t c,
+                                               double2 pc, double2 dh_c, double Nc, double inv_m2, int F,
+                                               bool* bad) {
+  const double2 pb = acc.at1(k, dir);
+  double fac = 0.0;
+  if (f.bc != BC_L0) {
+    const double Nb = fma(f.s, norm2(pb), -ldv<double>(f.V, c + dir * f.st[k]));
+    if (f.bc == BC_DIRICHLET) fac = -f.h2_over_a * Nb;
+    else fac = fma(f.h2_over_a, Nc - Nb, fma(dh_c.x, pc.x, dh_c.y * pc.y) * inv_m2);
+  }
+  const longlong2 pbf = acc.fx1(k, dir), pcf = acc.fx0(), fp = fix2(make_double2(fac * pb.x, fac * pb.y), F);
+  bool b = fbad(pbf) | fbad(pcf) | fbad(fp);
+  long long gx = 2 * D * pbf.x + fp.x - pcf.x, gy = 2 * D * pbf.y + fp.y - pcf.y;
+#pragma unroll
+  for (int j = 0; j < D; ++j) {
+    if (j == k) continue;
+    const longlong2 u = acc.fx2(k, dir, j, 1), w = acc.fx2(k, dir, j, -1);
+    b |= fbad(u) | fbad(w);
+    gx -= u.x + w.x;
+    gy -= u.y + w.y;
+  }
+  *bad |= b;
+  return make_longlong2(gx, gy);
+}
+
 // s2 = sum over axes of Psi_{+2} + Psi_{-2} in fixed point at a site next to a
-// wall, with the ghosts (computed in FP64 like the FP64 stencil) in place of
-// the values beyond the wall.  Out of line: only wall-adjacent sites call it.
+// wall, with the fixed-point ghosts in place of the values beyond the wall.
+// dh_c (h^2 D_c) comes from the exact integer sums of the face neighbours.
+// Out of line: only wall-adjacent sites call it.
 template <class T, int D, class Acc>
 __device__ __forceinline__ longlong2 exact_s2_wall(const Field<T>& f, const Acc& acc, const int* idx, int64_t c,
-                                                double2 pc, double Nc, int F, bool* bad) {
-  double2 t = {0.0, 0.0};
-#pragma unroll
-  for (int k = 0; k < D; ++k) {
-    const double2 u = acc.at1(k, 1), w = acc.at1(k, -1);
-    t.x += u.x + w.x;
-    t.y += u.y + w.y;
-  }
-  const double2 dh = {fma(double(-2 * D), pc.x, t.x), fma(double(-2 * D), pc.y, t.y)};   // h^2 D_c in FP64
+                                                double2 pc, double2 dh, double Nc, double inv_m2, int F,
+                                                bool* bad) {
   long long sx = 0, sy = 0;
   bool b = false;
 #pragma unroll
   for (int k = 0; k < D; ++k) {
     longlong2 lo, hi;
     if (idx[k] >= 2) lo = acc.fx1(k, -2);
-    else lo = fix2(ghost<T, D>(f, acc, k, -1, c, pc, dh, Nc), F);
+    else lo = ghost_fix<T, D>(f, acc, k, -1, c, pc, dh, Nc, inv_m2, F, &b);
     if (idx[k] <= f.n[k] - 3) hi = acc.fx1(k, 2);
-    else hi = fix2(ghost<T, D>(f, acc, k, 1, c, pc, dh, Nc), F);
+    else hi = ghost_fix<T, D>(f, acc, k, 1, c, pc, dh, Nc, inv_m2, F, &b);
     b |= fbad(lo) | fbad(hi);
     sx += lo.x + hi.x;
     sy += lo.y + hi.y;
@@ -325,9 +352,9 @@ __device__ __forceinline__ double i2d_rn(long long v, int eadj = 0) {
 // outside the fixed-point range take the FP64 stencil, rescaled.
 template <class T, int D, int ORDER, class Acc>
 __device__ __forceinline__ double2 a_lap_exact(const Field<T>& f, const Acc& acc, const int* idx, int64_t c,
-                                               double2 pc, double Ng) {
+                                               double2 pc, double Ng, double inv_m2) {
   static_assert(std::is_same<typename T::R, double>::value, "exact-sum stencil is FP64 only");
-  const int F = cur_fix(f), eadj = f.F - F;
+  const int F = acc.fixF(), eadj = f.F - F;
   const longlong2 cc = acc.fx0();
   bool bad = fbad(cc);
   long long s1x = 0, s1y = 0;
@@ -357,7 +384,9 @@ __device__ __forceinline__ double2 a_lap_exact(const Field<T>& f, const Acc& acc
       s2y += lo.y + hi.y;
     }
   } else {
-    const longlong2 s2 = exact_s2_wall<T, D>(f, acc, idx, c, pc, Nc, F, &bad);
+    // h^2 D_c from the exact face-neighbour sum (the MSD ghosts' ratio term needs it)
+    const double2 dh = {i2d_rn(s1x - 2 * D * cc.x, -F), i2d_rn(s1y - 2 * D * cc.y, -F)};
+    const longlong2 s2 = exact_s2_wall<T, D>(f, acc, idx, c, pc, dh, Nc, inv_m2, F, &bad);
     s2x = s2.x;
     s2y = s2.y;
   }
@@ -375,7 +404,7 @@ __device__ __forceinline__ double2 a_lap_exact(const Field<T>& f, const Acc& acc
 template <class T, int D, int ORDER, class Acc>
 __device__ __forceinline__ double2 a_lap_exact_deep(const Field<T>& f, const Acc& acc, const int* idx, int64_t c,
                                                     double2 pc, double Ng) {
-  const int eadj = f.F - cur_fix(f);
+  const int eadj = f.F - acc.fixF();
   const longlong2 cc = acc.fx0();
   bool bad = fbad(cc);
   long long s1x = 0, s1y = 0;
@@ -417,6 +446,10 @@ __device__ __forceinline__ longlong2 GAcc<T, D>::fx0() const { return fix2(ld2<d
 template <class T, int D>
 __device__ __forceinline__ longlong2 GAcc<T, D>::fx1(int k, int s) const {
   return fix2(ld2<double>(f.in, c + s * f.st[k]), cur_fix(f));
+}
+template <class T, int D>
+__device__ __forceinline__ longlong2 GAcc<T, D>::fx2(int k, int s, int j, int t) const {
+  return fix2(ld2<double>(f.in, c + s * f.st[k] + t * f.st[j]), cur_fix(f));
 }
 
 // Everything a stage writes, on top of the field it reads.
@@ -550,15 +583,20 @@ __device__ __forceinline__ unsigned int rk_update(const StageArgs<T>& A, int64_t
 // Out of line: only sites next to a wall call it.
 template <class T, int D, bool EXACT, class Acc>
 __device__ __forceinline__ unsigned int serve_walls(const StageArgs<T>& A, const Acc& acc, const int* idx, int64_t c,
-                                                 typename V2<typename T::R>::t pc, typename V2<typename T::R>::t F) {
+                                                 typename V2<typename T::R>::t pc, typename V2<typename T::R>::t F,
+                                                 typename T::R inv_m2) {
   using R = typename T::R;
   using C2 = typename V2<R>::t;
   const Field<T>& f = A.f;
   R theta = R(0);
   unsigned int ex = 0;
   if (f.bc == BC_MSD) {
-    const R m2 = norm2(pc);
-    if (m2 > f.tiny) theta = fma(F.y, pc.x, -(F.x * pc.y)) / m2;
+    if constexpr (EXACT) {   // the site's reciprocal 1 / |Psi_c|^2 (0 below the guard), shared with its ghosts
+      theta = fma(F.y, pc.x, -(F.x * pc.y)) * inv_m2;
+    } else {
+      const R m2 = norm2(pc);
+      if (m2 > f.tiny) theta = fma(F.y, pc.x, -(F.x * pc.y)) / m2;
+    }
   }
   // all offsets o in {-1, 0, 1}^D except 0, where -1 needs idx == 1 and +1 needs idx == n - 2
 #pragma unroll
@@ -602,8 +640,15 @@ __device__ __forceinline__ unsigned int process_site_pv(const StageArgs<T>& A, c
   const C2 pc = acc.at0();
   // exact-sum stages work in units of cLF: Nc / cLF (p.v holds V / cLF there)
   const R Nc = fma(EXACT ? f.sG : f.s, norm2(pc), -p.v);
+  R inv_m2 = R(0);
+  if constexpr (EXACT) {   // one reciprocal per MSD wall-adjacent site, for its ghosts and its walls' theta
+    if (f.bc == BC_MSD && near_wall2<D>(idx, f.n)) {
+      const R m2 = norm2(pc);
+      inv_m2 = (m2 > f.tiny) ? R(1) / m2 : R(0);
+    }
+  }
   C2 aL;
-  if constexpr (EXACT) aL = a_lap_exact<T, D, ORDER>(f, acc, idx, c, pc, Nc);
+  if constexpr (EXACT) aL = a_lap_exact<T, D, ORDER>(f, acc, idx, c, pc, Nc, inv_m2);
   else aL = a_lap<T, D, ORDER>(f, acc, idx, c, pc, Nc);
   const C2 F = {-fma(Nc, pc.y, aL.y), fma(Nc, pc.x, aL.x)};
   unsigned int ex = rk_apply<T>(A, c, F, p);
@@ -611,7 +656,7 @@ __device__ __forceinline__ unsigned int process_site_pv(const StageArgs<T>& A, c
   bool near = false;
 #pragma unroll
   for (int k = 0; k < D; ++k) near |= (idx[k] == 1) | (idx[k] == f.n[k] - 2);
-  if (near) ex = max(ex, serve_walls<T, D, EXACT>(A, acc, idx, c, pc, F));
+  if (near) ex = max(ex, serve_walls<T, D, EXACT>(A, acc, idx, c, pc, F, inv_m2));
   return ex;
 }
 
@@ -652,22 +697,29 @@ struct GAccP {
   __device__ __forceinline__ longlong2 fx1(int k, int s) const {
     return fix2(ld2<double>(f.in, c + sh(k, s)), cur_fix(f));
   }
+  __device__ __forceinline__ int fixF() const { return cur_fix(f); }
 };
 
-// F and the stage update at site c (multi-index idx) of a periodic grid.
-template <class T, int D, int ORDER, bool EXACT>
-__device__ __forceinline__ unsigned int process_site_periodic(const StageArgs<T>& A, const int* idx, int64_t c) {
+// F and the stage update at site c (multi-index idx) of a periodic grid, the
+// operands from an accessor whose neighbours wrap.
+template <class T, int D, int ORDER, bool EXACT, class Acc>
+__device__ __forceinline__ unsigned int process_site_periodic_acc(const StageArgs<T>& A, const Acc& acc,
+                                                                  const int* idx, int64_t c) {
   using R = typename T::R;
   using C2 = typename V2<R>::t;
   const Field<T>& f = A.f;
-  const GAccP<T, D> acc(f, c, idx);
   const PointVals<T> p = load_point<T, -1, EXACT>(A, c, true);
   const C2 pc = acc.at0();
   const R Nc = fma(EXACT ? f.sG : f.s, norm2(pc), -p.v);   // units of cLF on the exact-sum stages
   C2 aL;
   if constexpr (EXACT) aL = a_lap_exact_deep<T, D, ORDER>(f, acc, idx, c, pc, Nc);
-  else aL = a_lap_body<T, D, ORDER, GAccP<T, D>, false>(f, acc, idx, c, pc, Nc);
+  else aL = a_lap_body<T, D, ORDER, Acc, false>(f, acc, idx, c, pc, Nc);
   return rk_apply<T>(A, c, {-fma(Nc, pc.y, aL.y), fma(Nc, pc.x, aL.x)}, p);
+}
+
+template <class T, int D, int ORDER, bool EXACT>
+__device__ __forceinline__ unsigned int process_site_periodic(const StageArgs<T>& A, const int* idx, int64_t c) {
+  return process_site_periodic_acc<T, D, ORDER, EXACT>(A, GAccP<T, D>(A.f, c, idx), idx, c);
 }
 
 // How a stage is launched: kernel variant, CTA tile, and (3D tiled kernel)

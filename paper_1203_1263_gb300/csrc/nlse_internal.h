@@ -29,6 +29,15 @@ bool fused_grid_ok(int d, const int* n);
 // the fused kernel's TMA box: 64 + 8 complex values by 8 + 8 rows
 constexpr int kFusedBoxX = 2 * (64 + 8), kFusedBoxY = 8 + 8;
 
+// 1D lines on one thread-block cluster (stage_line1d.cuh): nsteps RK4 steps of
+// an n-site line in one launch; A[0..3] are stages 1..4 with Psi updated in
+// place.  cudaErrorInvalidConfiguration when the line does not fit or the
+// cluster cannot be co-scheduled (the caller then takes the per-site kernel).
+bool line_ok(int n, bool fp64);
+template <class T>
+cudaError_t launch_line_steps(const StageArgs<T>* A, int64_t nsteps, int n, int order, bool exact, int F0,
+                              int fix_offset, cudaStream_t stream);
+
 cudaError_t launch_mass(const void* psi, bool psi_double, int64_t total, double scale, double* partials,
                         double* result, unsigned int* flag, cudaStream_t stream);
 template <class T, int D, int ORDER>

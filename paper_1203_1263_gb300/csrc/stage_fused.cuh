@@ -102,9 +102,62 @@ __global__ void __launch_bounds__(TX* TYT, 2) k_stage3d_fused(const StageArgs<P3
   // ring slots by plane number: first-stage plane z in mid slot (z - z1b) mod 5, its tile K in slot mod 3
   auto mslot = [&](int z) { const int q = (z - z1b) % 5; return mid + (q < 0 ? q + 5 : q) * (G::kMid / sizeof(float2)); };
   auto kslot = [&](int z) { const int q = (z - z1b) % 3; return kr + (q < 0 ? q + 3 : q) * (G::kK / sizeof(float2)); };
+
+  // This thread's first-stage sites (the same (x, y) on every plane): element e = tid + k NT of the
+  // tile-plus-halo region, needed when at least two cells from the x and y walls.
+  constexpr int NS1 = (G::PS2 + NT - 1) / NT;
+  int s1o[NS1], s1k[NS1];         // element in the input plane; tile position (cy TX + cx) or -1
+  int64_t s1c[NS1];               // column offset gy nx + gx
+  bool s1ok[NS1];
+#pragma unroll
+  for (int k = 0; k < NS1; ++k) {
+    const int e = tid + k * NT;
+    const int ry = e / G::W2, rx = e - ry * G::W2;
+    const int gx = x0 - 2 + rx, gy = y0 - 2 + ry;
+    s1ok[k] = e < G::PS2 && in_deep(gx, nx, 2) && in_deep(gy, ny, 2);
+    s1o[k] = (ry + 2) * G::W4 + rx + 2;
+    const int cx = rx - 2, cy = ry - 2;
+    s1k[k] = (cx >= 0 && cx < TX && cy >= 0 && cy < TY) ? cy * TX + cx : -1;
+    s1c[k] = (int64_t)gy * nx + gx;
+  }
+  // the pointwise operands the first stage reads from global memory, one plane ahead
+  float v1[NS1], v1n[NS1];
+  float2 pn1[NS1], pn1n[NS1], k1[NS1], k1n[NS1];
+  auto load1 = [&](int z, float* v, float2* pn, float2* kk) {
+#pragma unroll
+    for (int k = 0; k < NS1; ++k) {
+      if (!s1ok[k] || z >= z1e) continue;
+      const int64_t c = z * plane + s1c[k];
+      v[k] = with_v ? __ldg(f.V + c) : 0.f;
+      if (S1 == 3) {
+        pn[k] = __ldg(A1.psin + c);
+        if (s1k[k] >= 0) kk[k] = __ldg(A1.ktot + c);
+      }
+    }
+  };
+  // the second stage's sites and their operands (V; Psi^n for stage 4), one plane ahead
+  float v2[RY], v2n[RY];
+  float2 pn2[RY], pn2n[RY];
+  auto load2 = [&](int z) {
+#pragma unroll
+    for (int r = 0; r < RY; ++r) {
+      const int gx = x0 + threadIdx.x, gy = y0 + threadIdx.y + r * TYT;
+      if (!(z >= zb && z < ze && in_deep(z, nz, 4) && in_deep(gx, nx, 4) && in_deep(gy, ny, 4))) continue;
+      const int64_t c = z * plane + (int64_t)gy * nx + gx;
+      v2n[r] = with_v ? __ldg(f.V + c) : 0.f;
+      if (S1 == 3) pn2n[r] = __ldg(A1.psin + c);
+    }
+  };
+  load1(z1b, v1, pn1, k1);
+  load2(z1b - 2);
+#pragma unroll
+  for (int r = 0; r < RY; ++r) { v2[r] = v2n[r]; pn2[r] = pn2n[r]; }
+
   bool aborted = false;
   // iteration z1: the first stage at plane z1 (while z1 < z1e), then the second stage at plane z1 - 2
   for (int z1 = z1b; z1 < ze + 2; ++z1) {
+    load1(z1 + 1, v1n, pn1n, k1n);   // next plane's operands in flight during this plane's work
+    load2(z1 - 1);
     // ---- first stage at plane z1, tile + two-cell halo ----
     if (z1 < z1e) {
       late |= !mbar_wait_bounded(smem_u32(bars + wslot), wpar, spin_limit);
@@ -112,32 +165,27 @@ __global__ void __launch_bounds__(TX* TYT, 2) k_stage3d_fused(const StageArgs<P3
       if (++wslot == RS) { wslot = 0; wpar ^= 1u; }
       float2* mplane = mslot(z1);
       float2* kplane = kslot(z1);
-      for (int e = tid; e < G::PS2 && !late; e += NT) {
-        const int ry = e / G::W2, rx = e - ry * G::W2;
-        const int gx = x0 - 2 + rx, gy = y0 - 2 + ry;
-        if (!(in_deep(gx, nx, 2) && in_deep(gy, ny, 2))) continue;   // not needed by any second-stage site
-        const int64_t c = z1 * plane + (int64_t)gy * nx + gx;
+#pragma unroll
+      for (int k = 0; k < NS1; ++k) {
+        if (!s1ok[k] || late) continue;
+        const int e = tid + k * NT;
+        const int64_t c = z1 * plane + s1c[k];
         SAcc3<P32> acc;
 #pragma unroll
         for (int d = 0; d < 5; ++d) acc.p[d] = pl[d];
         acc.w = G::W4;
-        acc.o = (ry + 2) * G::W4 + rx + 2;
-        const int idx[3] = {z1, gy, gx};
+        acc.o = s1o[k];
+        const int idx[3] = {z1, 0, 0};   // unused by the wall-free stencil
         const float2 pc = acc.at0();
-        const float v = with_v ? __ldg(f.V + c) : 0.f;
-        const float Nc = fmaf(f.s, norm2(pc), -v);
+        const float Nc = fmaf(f.s, norm2(pc), -v1[k]);
         const float2 aL = a_lap_body<P32, 3, ORDER, SAcc3<P32>, false>(f, acc, idx, c, pc, Nc);
         const float2 F = {-fmaf(Nc, pc.y, aL.y), fmaf(Nc, pc.x, aL.x)};
-        const float2 pn = (S1 == 1) ? pc : __ldg(A1.psin + c);     // Psi^n
+        const float2 pn = (S1 == 1) ? pc : pn1[k];     // Psi^n
         mplane[e] = make_float2(fmaf(A1.dtc, F.x, pn.x), fmaf(A1.dtc, F.y, pn.y));
-        const int cx = rx - 2, cy = ry - 2;
-        if (cx >= 0 && cx < TX && cy >= 0 && cy < TY) {     // a tile site: keep its K for the second stage
+        if (s1k[k] >= 0) {     // a tile site: keep its K for the second stage
           float2 K = F;
-          if (S1 == 3) {
-            const float2 k0 = __ldg(A1.ktot + c);
-            K = make_float2(fmaf(2.f, F.x, k0.x), fmaf(2.f, F.y, k0.y));
-          }
-          kplane[cy * TX + cx] = K;
+          if (S1 == 3) K = make_float2(fmaf(2.f, F.x, k1[k].x), fmaf(2.f, F.y, k1[k].y));
+          kplane[s1k[k]] = K;
         }
       }
     }
@@ -175,13 +223,13 @@ __global__ void __launch_bounds__(TX* TYT, 2) k_stage3d_fused(const StageArgs<P3
         acc.o = o2;
         const int idx[3] = {z2, gy, gx};
         PointVals<P32> pv;
-        pv.v = with_v ? __ldg(f.V + c) : 0.f;
+        pv.v = v2[r];
         const float2 pc = acc.at0();
         const float Nc = fmaf(A2.f.s, norm2(pc), -pv.v);
         const float2 aL = a_lap_body<P32, 3, ORDER, SAcc3<P32>, false>(A2.f, acc, idx, c, pc, Nc);
         pv.K = K;
         if (S1 == 1) pv.pn = pl[0][(cy + 4) * G::W4 + cx + 4];   // Psi^n at plane z2 = z1 - 2: input ring plane 0
-        else pv.mst = __ldg(A1.psin + c);
+        else pv.mst = pn2[r];
         rk_apply<P32, S1 + 1>(A2, c, {-fmaf(Nc, pc.y, aL.y), fmaf(Nc, pc.x, aL.x)}, pv);
       }
     }
@@ -191,6 +239,10 @@ __global__ void __launch_bounds__(TX* TYT, 2) k_stage3d_fused(const StageArgs<P3
     }
 #pragma unroll
     for (int d = 0; d < 4; ++d) pl[d] = pl[d + 1];     // pl[0] is plane z1 - 1 from here on
+#pragma unroll
+    for (int k = 0; k < NS1; ++k) { v1[k] = v1n[k]; pn1[k] = pn1n[k]; k1[k] = k1n[k]; }
+#pragma unroll
+    for (int r = 0; r < RY; ++r) { v2[r] = v2n[r]; pn2[r] = pn2n[r]; }
     if (tid == 0 && z1 < z1e && issued < jl) issue(issued + 1);   // the slot of plane z1 - 2 is free now
   }
   if (aborted && tid == 0) {
@@ -219,9 +271,23 @@ cudaError_t launch_fused_kernel(const StageArgs<P32>& A1, const StageArgs<P32>& 
   const int nz = A1.f.n[0], ny = A1.f.n[1], nx = A1.f.n[2];
   const int tiles = ((nx + TX - 1) / TX) * ((ny + TY - 1) / TY);
   const int planes = nz - 4;
-  int nzc = (152 * 4 + tiles - 1) / tiles;
-  if (nzc > planes) nzc = planes;
-  if (nzc < 1) nzc = 1;
+  // z chunks: the count whose waves (two CTAs per SM) times planes per CTA (plus the six extra planes a
+  // chunk's rings fill and drain) is least, so that the last wave is not a short one
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0, v = 0;
+    sms = (cudaGetDevice(&dev) == cudaSuccess &&
+           cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0) ? v : 152;
+  }
+  const int slots = 2 * sms;
+  int nzc = 1;
+  long long best = -1;
+  for (int c = 1; c <= planes && c <= 64; ++c) {
+    const int zc_c = (planes + c - 1) / c;
+    const long long waves = ((long long)tiles * c + slots - 1) / slots;
+    const long long cost = waves * (zc_c + 6);
+    if (best < 0 || cost < best) { best = cost; nzc = c; }
+  }
   const int zc = (planes + nzc - 1) / nzc;
   nzc = (planes + zc - 1) / zc;
   const size_t smem = fused_smem_bytes();

@@ -50,6 +50,11 @@ struct SlabAcc {
     const C v = k == AXM ? p[2 + s][o] : p[2][o + off(k, s)];
     return fix2(make_double2(v.x, v.y), F);
   }
+  __device__ __forceinline__ longlong2 fx2(int k, int s, int j, int t) const {
+    const C2 v = at2(k, s, j, t);
+    return fix2(make_double2(v.x, v.y), F);
+  }
+  __device__ __forceinline__ int fixF() const { return F; }
 };
 
 struct SlabRange {

@@ -151,6 +151,24 @@ def test_256x256x512_laplacian_zero_boundary_full_size():
         g.close()
 
 
+def test_256x256x512_periodic_full_size():
+    """The benchmark's grid, potential and launch configuration on a periodic
+    grid (the boundary of the stability analysis, Sec. 3.4), on the trap
+    state plus a unit plane wave (so that the wrap carries a field): one step
+    against the oracle on every site, FP64 and FP32."""
+    p = W.trap_vortex_3d(shape=(512, 256, 256))
+    x = (np.arange(p.shape[2]) - 0.5 * (p.shape[2] - 1)) * p.h
+    psi0 = p.psi0 + 0.5 * np.exp(0.4j * x)[None, None, :]
+    s_rho = abs(p.s) * float(np.max(np.abs(psi0))) ** 2
+    dt = 0.8 * O.stability_bound(3, p.h, p.a, 4, p.vmax(), s_rho)
+    ref = O.rk4(psi0, p.h, p.a, p.s, dt, 1, p.V, W.BC_PERIODIC, 4)
+    for dtype, tol in (("c128", 1e-12), ("c64", 2e-5)):
+        g = Integrator(psi0, p.h, p.a, p.s, p.V, "periodic", 4, dtype)
+        g.step(1, dt)
+        assert rel_l2(g.numpy(), ref) <= tol, dtype
+        g.close()
+
+
 RINGS_DT = 0.8 * O.stability_bound(3, 0.25, 0.5, 4, 0.0, 1.0)   # the 512^3 grid's step (max|Psi0| = 1)
 
 

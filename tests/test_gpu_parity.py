@@ -177,6 +177,32 @@ def test_tiled_kernel_equals_generic_bitwise(dtype, dims, shape, tile_cfg):
             assert np.array_equal(res[2], res[3]), (order, bc)
 
 
+@pytest.mark.parametrize("n", [37, 1000, 2001, 5003, 60000])
+@pytest.mark.parametrize("bc", ["dirichlet", "msd", "l0", "periodic"])
+@pytest.mark.parametrize("order", [2, 4])
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_line_cluster_equals_per_site_bitwise(n, bc, order, dtype):
+    """1D: the thread-block-cluster path (the whole call in one launch, the
+    line in shared memory) gives the per-site kernel's bits, also when the
+    steps are split across calls; lines too long for shared memory (60,000
+    sites in FP64) take the per-site kernel."""
+    psi, V = problem((n,), 65, bc=bc)
+    h, a, s = 0.3, 0.6, -1.0
+    dt = stable_dt((n,), h, a, s, order, V)
+    per_site, line = (3, 2) if dtype == "c128" else (0, 1)
+    res = []
+    for variant, split in ((per_site, (21,)), (line, (21,)), (line, (5, 16))):
+        g = Integrator(psi, h, a, s, V, bc, order, dtype)
+        g.set_kernel(variant)
+        fits = not (dtype == "c128" and n > 49152)
+        assert g.kernel_in_use() == (line if variant == line and fits else per_site)
+        for k in split:
+            g.step(k, dt)
+        g.sync()
+        res.append(g.numpy())
+    assert np.array_equal(res[0], res[1]) and np.array_equal(res[1], res[2])
+
+
 FUSED_SHAPES = [(16, 16, 16), (20, 24, 70), (33, 40, 64), (40, 37, 130), (18, 70, 66), (20, 24, 71)]
 
 
