@@ -112,9 +112,37 @@ def bf16_peak():
 
 
 # FP64 peak of a GB300: 152 SMs x 2 FP64 FMA lanes per cycle x 2 flops at the
-# 2070 MHz maximum clock = 1.26 TFLOP/s (the recipe's nominal 1.25); measured
-# with independent DFMA chains on the GB300s: 0.998 TFLOP/s.
-FP64_PEAK_TFLOPS_MEASURED = 0.998
+# 2070 MHz maximum clock = 1.26 TFLOP/s nominal.  The figure the FP64 view is
+# taken against is measured live (fp64_peak) before the timed region.
+FP64_PEAK_NOMINAL = 1.26
+_FP64_PEAK = None
+
+
+def fp64_peak():
+    """Dense FP64 throughput of this GPU (TFLOP/s) and how it was obtained: cuBLAS DGEMM 4096^3
+    (2 N^3 flops), best of 3 after one warm-up, timed with CUDA events; the nominal figure if no GPU."""
+    global _FP64_PEAK
+    if _FP64_PEAK is None:
+        try:
+            import torch
+            n = 4096
+            a = torch.randn(n, n, dtype=torch.float64, device="cuda")
+            b = torch.randn(n, n, dtype=torch.float64, device="cuda")
+            torch.matmul(a, b)
+            best = None
+            for _ in range(3):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                torch.matmul(a, b)
+                e1.record()
+                e1.synchronize()
+                t = e0.elapsed_time(e1) * 1e-3
+                best = t if best is None else min(best, t)
+            del a, b
+            _FP64_PEAK = (2.0 * n ** 3 / best / 1e12, "measured live: cuBLAS DGEMM 4096^3, best of 3")
+        except Exception:   # no GPU: the nominal figure
+            _FP64_PEAK = (FP64_PEAK_NOMINAL, "nominal (152 SMs x 2 FP64 FMA lanes x 2 flops x 2070 MHz)")
+    return _FP64_PEAK
 
 
 def roofline_for(dtype, sites, step_s, with_v):
@@ -129,9 +157,9 @@ def roofline_for(dtype, sites, step_s, with_v):
            "alg_bytes_per_site_step": bytes_site}
     if dtype == "c128":
         tflops = sites * FP64_FLOPS_PER_SITE_STEP / step_s / 1e12
-        hbm["fp64_pipe_view"] = {"achieved": round(tflops, 4), "peak": FP64_PEAK_TFLOPS_MEASURED, "unit": "TFLOP/s",
-                                 "frac": round(tflops / FP64_PEAK_TFLOPS_MEASURED, 4),
-                                 "peak_kind": "measured with an FP64 FMA probe on this pool's GB300s",
+        pk, pk_kind = fp64_peak()
+        hbm["fp64_pipe_view"] = {"achieved": round(tflops, 4), "peak": round(pk, 4), "unit": "TFLOP/s",
+                                 "frac": round(tflops / pk, 4), "peak_kind": pk_kind,
                                  "flops_per_site_step": FP64_FLOPS_PER_SITE_STEP}
     return hbm
 
@@ -827,7 +855,7 @@ def main():
     ap.add_argument("--repeats", type=int, default=5, help="timed repeats of K steps (the first is the value)")
     ap.add_argument("--no-rings", dest="rings", action="store_false",
                     help="skip the 512^3 precision-form leg")
-    ap.add_argument("--sur-mass-weight", type=float, default=10.0,
+    ap.add_argument("--sur-mass-weight", type=float, default=0.0,
                     help="weight of the mass-conservation term of the surrogate's training loss")
     ap.add_argument("--ref-budget", type=float, default=90.0)
     args = ap.parse_args()

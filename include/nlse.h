@@ -174,13 +174,14 @@ const char *nlse_last_error(void);
  * Default: 2 for NLSE_C128 and 1 otherwise, except 3D grids of at most 2^18
  * sites (NLSE_C128) or 2^21 sites (the FP32 forms), which take 3 and 0.
  * The exact-sum stencil's fixed-point scale follows the state: before every
- * step it is taken from the largest component of Psi (so that every
- * component has 8x headroom below the 64-bit range), at the start of each
- * nlse_step from a pass over Psi (the caller may have written it) and after
- * each step from the values the step wrote; a site whose operand is still
- * out of range (a state that grew more than 8x within one step) takes the
- * FP64 stencil.  The resolution is thus 2^-50 or finer relative to max|Psi|
- * for any state, and results never depend on how steps are split into calls.
+ * step it is taken from the largest component of Psi (every component
+ * below 2^53 in fixed point, 4x below the accepted range, so the largest
+ * components keep all 53 bits), at the start of each nlse_step from a pass
+ * over Psi (the caller may have written it) and after each step from the
+ * values the step wrote; a site whose operand is still out of range (a
+ * stage state more than 4x the step's largest component) takes the FP64
+ * stencil.  The resolution is thus 2^-52 or finer relative to max|Psi| for
+ * any state, and results never depend on how steps are split into calls.
  *   4 = NLSE_C64 on 3D grids: two RK4 stages per pass (stages 1+2 and 3+4,
  *       temporal blocking): the first stage's result for a tile plus a
  *       two-cell halo stays on chip and feeds the second stage, so the

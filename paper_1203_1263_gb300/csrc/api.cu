@@ -533,9 +533,9 @@ int nlse_create(nlse_t* out, int dims, const int64_t* N, double h, double a, dou
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming);
   }
-  // Exact-sum stencil scale: operands must satisfy |v| < 2^(54 - F); take the
-  // largest component of Psi0 with 8x headroom for growth.
-  c->fixF = 50;
+  // Exact-sum stencil reference scale F0: the largest component of Psi0 below
+  // 2^53 in fixed point (operands are accepted below 2^55).
+  c->fixF = 52;
   if (e == cudaSuccess && dtype == NLSE_C128) {
     e = launch_vmax(psi, true, 2 * total, c->vbits(), c->stream);
     unsigned long long bits = 0;
@@ -546,7 +546,7 @@ int nlse_create(nlse_t* out, int dims, const int64_t* N, double h, double a, dou
     if (pmax > 0.0 && isfinite(pmax)) {
       int ex = 0;
       frexp(pmax, &ex);              // pmax < 2^ex
-      c->fixF = 54 - (ex + 3);
+      c->fixF = 56 - (ex + 3);
     }
   }
   if (e == cudaSuccess && dtype == NLSE_C128 && V) {   // V / cLF for the exact-sum stages

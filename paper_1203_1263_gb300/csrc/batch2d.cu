@@ -271,6 +271,7 @@ int upload_tables(nlse_batch* b) {
       A.ktot = ktot;
       A.out = outs[s];
       A.master = (float2*)d.psi;
+      A.master_in = (const float2*)d.psi;   // Psi updated in place: stage 4 reads Psi^n where it writes
       A.dtc = float(dtc[s]);
       A.dt6 = d.dt / 6.0;
       A.stage = s + 1;

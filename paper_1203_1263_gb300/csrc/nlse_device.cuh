@@ -214,10 +214,16 @@ __device__ __forceinline__ typename V2<typename T::R>::t a_lap(const Field<T>& f
 // stencil operand is converted (on the integer pipe, from its IEEE-754 bits)
 // to a 64-bit fixed-point number v * 2^F rounded to nearest; the sums
 // 16 s1 - s2 - 30 d Psi_c (or s1 - 2d Psi_c) are then exact integers, and one
-// conversion and one multiply by cL 2^-F give a*Lap in FP64.  F is chosen per
-// context so that |v| < 2^(54-F) covers the state with headroom; an operand
-// outside that range (or Inf/NaN) yields kFixBad and the site falls back to
-// the FP64 stencil, so the result is always defined.
+// conversion and one multiply by cL 2^-F give a*Lap in FP64.  An operand is
+// accepted while |v| 2^F < 2^55; F follows the state so that its largest
+// component stays below 2^53 (4x headroom for the stages' intermediate
+// states), which keeps all 53 bits of the largest components.  An operand
+// outside the range (or Inf/NaN) yields kFixBad and the site falls back to
+// the FP64 stencil, so the result is always defined.  Bounds of the sums
+// (L = 2^55): a deep site's 16 s1 - s2 - 30 d Psi_c stays below 64 d L
+// <= 192 L; a wall ghost is used only while below 2^57 = 4L (else the site
+// falls back), so a wall site's sum stays below (32 d + 8 d + 30 d) L <= 210 L;
+// both are below 2^63 = 256 L.
 // ---------------------------------------------------------------------------
 constexpr long long kFixBad = (long long)0x8000000000000000ull;
 
@@ -228,7 +234,7 @@ __device__ __forceinline__ long long fix1(double v, int F) {
   const int sh = e - 1075 + F;
   long long r;
   if (e == 0) return 0;                 // zero or subnormal: below any usable resolution
-  if (sh > 1) return kFixBad;           // out of range, or Inf / NaN (e = 2047)
+  if (sh > 2) return kFixBad;           // out of range (|v| 2^F >= 2^55), or Inf / NaN (e = 2047)
   if (sh >= 0) r = m << sh;
   else if (sh >= -54) { const int k = -sh; r = (m + (1ll << (k - 1))) >> k; }
   else r = 0;
@@ -238,7 +244,7 @@ __device__ __forceinline__ longlong2 fix2(double2 v, int F) { return make_longlo
 
 // The fraction bits the exact-sum stencil uses for the current state: F is
 // re-derived on the device before every step from the largest component of
-// Psi^n (|v| < 2^(54 - F) with 8x headroom), so the fixed-point resolution
+// Psi^n (|v| 2^F < 2^53, 4x below the accepted range), so the fixed-point resolution
 // 2^-F always follows the state's own scale.  The stencil sums are formed at
 // that scale and converted to units of cLF = cL 2^-F0 (F0: the reference
 // scale fixed at creation) by an exact power-of-two exponent shift.
@@ -267,18 +273,18 @@ __device__ __forceinline__ double2 a_lap_slow(const Field<T>& f, const Acc& acc,
 // The ghost beyond the wall in fixed point (exact-sum stages): with fac = h^2 D_b / Psi_b (the boundary
 // Laplacian form, Eqs. BCDlap, BCMSDlap, BCL0lap) the ghost is g = 2d Psi_b + fac Psi_b - Psi_c -
 // sum_{in-face neighbours of b} Psi (see ghost()); only fac and fac Psi_b are formed in FP64, the rest of
-// the sum is exact in fixed point.  dh_c = h^2 D_c and inv_m2 = 1 / |Psi_c|^2 (0 below the MSD guard)
+// the sum is exact in fixed point.  dh_c = h^2 D_c and m2 = |Psi_c|^2 (0 below the MSD guard)
 // come from the caller, once per site.
 template <class T, int D, class Acc>
 __device__ __forceinline__ longlong2 ghost_fix(const Field<T>& f, const Acc& acc, int k, int dir, int64_t c,
-                                               double2 pc, double2 dh_c, double Nc, double inv_m2, int F,
+                                               double2 pc, double2 dh_c, double Nc, double m2, int F,
                                                bool* bad) {
   const double2 pb = acc.at1(k, dir);
   double fac = 0.0;
   if (f.bc != BC_L0) {
     const double Nb = fma(f.s, norm2(pb), -ldv<double>(f.V, c + dir * f.st[k]));
     if (f.bc == BC_DIRICHLET) fac = -f.h2_over_a * Nb;
-    else fac = fma(f.h2_over_a, Nc - Nb, fma(dh_c.x, pc.x, dh_c.y * pc.y) * inv_m2);
+    else fac = fma(f.h2_over_a, Nc - Nb, m2 > 0.0 ? fma(dh_c.x, pc.x, dh_c.y * pc.y) / m2 : 0.0);
   }
   const longlong2 pbf = acc.fx1(k, dir), pcf = acc.fx0(), fp = fix2(make_double2(fac * pb.x, fac * pb.y), F);
   bool b = fbad(pbf) | fbad(pcf) | fbad(fp);
@@ -291,6 +297,9 @@ __device__ __forceinline__ longlong2 ghost_fix(const Field<T>& f, const Acc& acc
     gx -= u.x + w.x;
     gy -= u.y + w.y;
   }
+  // |g| < 4 d 2^55 from its terms; beyond 2^57 the site takes the FP64 stencil (keeps the sum's bound)
+  constexpr long long kGhostMax = 1ll << 57;
+  b |= (gx >= kGhostMax) | (gx <= -kGhostMax) | (gy >= kGhostMax) | (gy <= -kGhostMax);
   *bad |= b;
   return make_longlong2(gx, gy);
 }
@@ -301,7 +310,7 @@ __device__ __forceinline__ longlong2 ghost_fix(const Field<T>& f, const Acc& acc
 // Out of line: only wall-adjacent sites call it.
 template <class T, int D, class Acc>
 __device__ __forceinline__ longlong2 exact_s2_wall(const Field<T>& f, const Acc& acc, const int* idx, int64_t c,
-                                                double2 pc, double2 dh, double Nc, double inv_m2, int F,
+                                                double2 pc, double2 dh, double Nc, double m2, int F,
                                                 bool* bad) {
   long long sx = 0, sy = 0;
   bool b = false;
@@ -309,9 +318,9 @@ __device__ __forceinline__ longlong2 exact_s2_wall(const Field<T>& f, const Acc&
   for (int k = 0; k < D; ++k) {
     longlong2 lo, hi;
     if (idx[k] >= 2) lo = acc.fx1(k, -2);
-    else lo = ghost_fix<T, D>(f, acc, k, -1, c, pc, dh, Nc, inv_m2, F, &b);
+    else lo = ghost_fix<T, D>(f, acc, k, -1, c, pc, dh, Nc, m2, F, &b);
     if (idx[k] <= f.n[k] - 3) hi = acc.fx1(k, 2);
-    else hi = ghost_fix<T, D>(f, acc, k, 1, c, pc, dh, Nc, inv_m2, F, &b);
+    else hi = ghost_fix<T, D>(f, acc, k, 1, c, pc, dh, Nc, m2, F, &b);
     b |= fbad(lo) | fbad(hi);
     sx += lo.x + hi.x;
     sy += lo.y + hi.y;
@@ -352,7 +361,7 @@ __device__ __forceinline__ double i2d_rn(long long v, int eadj = 0) {
 // outside the fixed-point range take the FP64 stencil, rescaled.
 template <class T, int D, int ORDER, class Acc>
 __device__ __forceinline__ double2 a_lap_exact(const Field<T>& f, const Acc& acc, const int* idx, int64_t c,
-                                               double2 pc, double Ng, double inv_m2) {
+                                               double2 pc, double Ng, double m2) {
   static_assert(std::is_same<typename T::R, double>::value, "exact-sum stencil is FP64 only");
   const int F = acc.fixF(), eadj = f.F - F;
   const longlong2 cc = acc.fx0();
@@ -386,7 +395,7 @@ __device__ __forceinline__ double2 a_lap_exact(const Field<T>& f, const Acc& acc
   } else {
     // h^2 D_c from the exact face-neighbour sum (the MSD ghosts' ratio term needs it)
     const double2 dh = {i2d_rn(s1x - 2 * D * cc.x, -F), i2d_rn(s1y - 2 * D * cc.y, -F)};
-    const longlong2 s2 = exact_s2_wall<T, D>(f, acc, idx, c, pc, dh, Nc, inv_m2, F, &bad);
+    const longlong2 s2 = exact_s2_wall<T, D>(f, acc, idx, c, pc, dh, Nc, m2, F, &bad);
     s2x = s2.x;
     s2y = s2.y;
   }
@@ -584,19 +593,17 @@ __device__ __forceinline__ unsigned int rk_update(const StageArgs<T>& A, int64_t
 template <class T, int D, bool EXACT, class Acc>
 __device__ __forceinline__ unsigned int serve_walls(const StageArgs<T>& A, const Acc& acc, const int* idx, int64_t c,
                                                  typename V2<typename T::R>::t pc, typename V2<typename T::R>::t F,
-                                                 typename T::R inv_m2) {
+                                                 typename T::R m2w) {
   using R = typename T::R;
   using C2 = typename V2<R>::t;
   const Field<T>& f = A.f;
   R theta = R(0);
   unsigned int ex = 0;
   if (f.bc == BC_MSD) {
-    if constexpr (EXACT) {   // the site's reciprocal 1 / |Psi_c|^2 (0 below the guard), shared with its ghosts
-      theta = fma(F.y, pc.x, -(F.x * pc.y)) * inv_m2;
-    } else {
-      const R m2 = norm2(pc);
-      if (m2 > f.tiny) theta = fma(F.y, pc.x, -(F.x * pc.y)) / m2;
-    }
+    // Im(F_c / Psi_c) = Im(F_c conj(Psi_c)) / |Psi_c|^2, 0 below the guard; the exact-sum stages pass
+    // |Psi_c|^2 in (m2w, already guarded), shared with the site's ghosts
+    const R m2 = EXACT ? m2w : norm2(pc);
+    if (EXACT ? m2 > R(0) : m2 > f.tiny) theta = fma(F.y, pc.x, -(F.x * pc.y)) / m2;
   }
   // all offsets o in {-1, 0, 1}^D except 0, where -1 needs idx == 1 and +1 needs idx == n - 2
 #pragma unroll
@@ -640,15 +647,15 @@ __device__ __forceinline__ unsigned int process_site_pv(const StageArgs<T>& A, c
   const C2 pc = acc.at0();
   // exact-sum stages work in units of cLF: Nc / cLF (p.v holds V / cLF there)
   const R Nc = fma(EXACT ? f.sG : f.s, norm2(pc), -p.v);
-  R inv_m2 = R(0);
-  if constexpr (EXACT) {   // one reciprocal per MSD wall-adjacent site, for its ghosts and its walls' theta
+  R m2w = R(0);
+  if constexpr (EXACT) {   // |Psi_c|^2 of an MSD wall-adjacent site (0 below the guard), for its ghosts and theta
     if (f.bc == BC_MSD && near_wall2<D>(idx, f.n)) {
       const R m2 = norm2(pc);
-      inv_m2 = (m2 > f.tiny) ? R(1) / m2 : R(0);
+      m2w = (m2 > f.tiny) ? m2 : R(0);
     }
   }
   C2 aL;
-  if constexpr (EXACT) aL = a_lap_exact<T, D, ORDER>(f, acc, idx, c, pc, Nc, inv_m2);
+  if constexpr (EXACT) aL = a_lap_exact<T, D, ORDER>(f, acc, idx, c, pc, Nc, m2w);
   else aL = a_lap<T, D, ORDER>(f, acc, idx, c, pc, Nc);
   const C2 F = {-fma(Nc, pc.y, aL.y), fma(Nc, pc.x, aL.x)};
   unsigned int ex = rk_apply<T>(A, c, F, p);
@@ -656,7 +663,7 @@ __device__ __forceinline__ unsigned int process_site_pv(const StageArgs<T>& A, c
   bool near = false;
 #pragma unroll
   for (int k = 0; k < D; ++k) near |= (idx[k] == 1) | (idx[k] == f.n[k] - 2);
-  if (near) ex = max(ex, serve_walls<T, D, EXACT>(A, acc, idx, c, pc, F, inv_m2));
+  if (near) ex = max(ex, serve_walls<T, D, EXACT>(A, acc, idx, c, pc, F, m2w));
   return ex;
 }
 

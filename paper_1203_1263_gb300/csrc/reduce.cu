@@ -154,15 +154,15 @@ __global__ void __launch_bounds__(256) k_max_expo(const double* __restrict__ v, 
 
 // Fraction bits of the exact-sum stencil for the state whose largest
 // component has biased exponent E (collected in *emax by k_max_expo or by
-// stage 4): |v| < 2^(E - 1022), so F = 54 - (E - 1022 + 3) = 1073 - E keeps
-// every component below 2^(54 - F) with 8x headroom.  A zero state keeps F0;
+// stage 4): |v| < 2^(E - 1022), so F = 1075 - E keeps every component below
+// 2^53 in fixed point, 4x below the accepted range 2^55.  A zero state keeps F0;
 // a non-finite one keeps the previous F (the non-finite flag reports it).
 // `offset` is a test hook (nlse_debug_set).  Resets *emax for the next step.
 __global__ void k_fix_update(unsigned int* emax, int* fdev, int F0, int offset) {
   if (threadIdx.x == 0 && blockIdx.x == 0) {
     const unsigned int E = *emax;
     if (E == 0u) *fdev = F0 + offset;
-    else if (E < 2047u) *fdev = 1073 - int(E) + offset;
+    else if (E < 2047u) *fdev = 1075 - int(E) + offset;
     *emax = 0u;
   }
 }

@@ -271,29 +271,18 @@ cudaError_t launch_fused_kernel(const StageArgs<P32>& A1, const StageArgs<P32>& 
   const int nz = A1.f.n[0], ny = A1.f.n[1], nx = A1.f.n[2];
   const int tiles = ((nx + TX - 1) / TX) * ((ny + TY - 1) / TY);
   const int planes = nz - 4;
-  // z chunks: the count whose waves (two CTAs per SM) times planes per CTA (plus the six extra planes a
-  // chunk's rings fill and drain) is least, so that the last wave is not a short one
-  static int sms = 0;
-  if (sms == 0) {
-    int dev = 0, v = 0;
-    sms = (cudaGetDevice(&dev) == cudaSuccess &&
-           cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0) ? v : 152;
-  }
-  const int slots = 2 * sms;
-  int nzc = 1;
-  long long best = -1;
-  for (int c = 1; c <= planes && c <= 64; ++c) {
-    const int zc_c = (planes + c - 1) / c;
-    const long long waves = ((long long)tiles * c + slots - 1) / slots;
-    const long long cost = waves * (zc_c + 6);
-    if (best < 0 || cost < best) { best = cost; nzc = c; }
-  }
-  const int zc = (planes + nzc - 1) / nzc;
-  nzc = (planes + zc - 1) / zc;
   const size_t smem = fused_smem_bytes();
   auto kern = k_stage3d_fused<ORDER, S1, TX, kFusedTYT, kFusedRY, kFusedP>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
+  static int per_sm = 0;
+  if (per_sm == 0) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    per_sm = resident_per_sm(kern, TX * kFusedTYT, smem);
+  }
+  // six extra planes: a chunk's rings fill and drain
+  int nzc = z_chunks(tiles, planes, per_sm, 6);
+  const int zc = (planes + nzc - 1) / nzc;
+  nzc = (planes + zc - 1) / zc;
   dim3 grid((nx + TX - 1) / TX, (ny + TY - 1) / TY, nzc);
   kern<<<grid, dim3(TX, kFusedTYT), smem, stream>>>(A1, A2, *tm, zc, spin_limit, extra_tx);
   return cudaGetLastError();

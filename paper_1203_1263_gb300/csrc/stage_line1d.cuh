@@ -59,7 +59,7 @@ struct LineArgs {
 // Fraction bits for the largest biased exponent E of the state (as k_fix_update).
 __device__ __forceinline__ int line_fix_from(unsigned int E, int Fprev, int F0, int offset) {
   if (E == 0u) return F0 + offset;
-  if (E < 2047u) return 1073 - int(E) + offset;
+  if (E < 2047u) return 1075 - int(E) + offset;
   return Fprev;
 }
 

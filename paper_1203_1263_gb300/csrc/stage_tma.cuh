@@ -72,6 +72,46 @@ struct TmaGeom {
   static constexpr uint32_t kSlot = (kBytes + 127u) / 128u * 128u;         // 128-byte aligned slots
 };
 
+// Number of z chunks for a z-marching kernel over `tiles` (x, y) tiles and
+// `planes` planes, `per_sm` CTAs resident per SM: the count whose waves times
+// planes per CTA (plus the `fill` planes a chunk's ring loads before its
+// first output plane) is least, so that no short last wave or overlong
+// chunk sets the kernel's time.  Results do not depend on the chunking: every
+// plane is computed by the same per-site code whichever CTA owns it.
+inline int z_chunks(int tiles, int planes, int per_sm, int fill) {
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0, v = 0;
+    sms = (cudaGetDevice(&dev) == cudaSuccess &&
+           cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0) ? v : 152;
+  }
+  const long long slots = (long long)(per_sm > 0 ? per_sm : 1) * sms;
+  int best_c = 1;
+  long long best = -1;
+  for (int c = 1; c <= planes && c <= 64; ++c) {
+    const int zc = (planes + c - 1) / c;
+    const long long waves = ((long long)tiles * c + slots - 1) / slots;
+    const long long cost = waves * (zc + fill);
+    if (best < 0 || cost < best) {
+      best = cost;
+      best_c = c;
+    }
+  }
+  return best_c;
+}
+
+// CTAs of `kern` resident per SM at `threads` threads and `smem` bytes of dynamic shared memory
+// (cached by the caller per kernel instantiation).
+template <class K>
+inline int resident_per_sm(K kern, int threads, size_t smem) {
+  int v = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, kern, threads, smem) != cudaSuccess || v < 1) {
+    cudaGetLastError();
+    v = 1;
+  }
+  return v;
+}
+
 template <class T, int ORDER, int S, int TX, int TYT, int RY, int P>
 __global__ void __launch_bounds__(TX* TYT) k_stage3d_tma(const StageArgs<T> A, const __grid_constant__ CUtensorMap tm,
                                                         int zc, long long spin_limit, uint32_t extra_tx) {
@@ -369,17 +409,19 @@ cudaError_t launch3d_tma_exact_shape(const StageArgs<T>& A, const CUtensorMap* t
   const int nz = A.f.n[0], ny = A.f.n[1], nx = A.f.n[2];
   const int tiles = ((nx + TX - 1) / TX) * ((ny + TY - 1) / TY);
   const int planes = nz - 2;
-  int nzc = (152 * 8 + tiles - 1) / tiles;
-  if (nzc > planes) nzc = planes;
-  if (nzc < 1) nzc = 1;
-  const int zc = (planes + nzc - 1) / nzc;
-  nzc = (planes + zc - 1) / zc;
   const size_t smem = (P + 1 + 6) * G::kSlot + (P + 1) * sizeof(uint64_t);
   auto kern = k_stage3d_tma_exact<T, ORDER, S, TX, TYT, RY, P>;
-  if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
+  static int per_sm = 0;
+  if (per_sm == 0) {
+    if (smem > 48 * 1024) {
+      cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+    }
+    per_sm = resident_per_sm(kern, TX * TYT, smem);
   }
+  int nzc = z_chunks(tiles, planes, per_sm, 4);
+  const int zc = (planes + nzc - 1) / nzc;
+  nzc = (planes + zc - 1) / zc;
   dim3 grid((nx + TX - 1) / TX, (ny + TY - 1) / TY, nzc);
   kern<<<grid, dim3(TX, TYT), smem, stream>>>(A, *tm, zc, spin_limit, extra_tx);
   return cudaGetLastError();
@@ -393,17 +435,19 @@ cudaError_t launch3d_tma_shape(const StageArgs<T>& A, const CUtensorMap* tm, lon
   const int nz = A.f.n[0], ny = A.f.n[1], nx = A.f.n[2];
   const int tiles = ((nx + TX - 1) / TX) * ((ny + TY - 1) / TY);
   const int planes = nz - 2;
-  int nzc = (152 * 8 + tiles - 1) / tiles;
-  if (nzc > planes) nzc = planes;
-  if (nzc < 1) nzc = 1;
-  const int zc = (planes + nzc - 1) / nzc;
-  nzc = (planes + zc - 1) / zc;
   const size_t smem = (5 + P) * G::kSlot + (5 + P) * sizeof(uint64_t);
   auto kern = k_stage3d_tma<T, ORDER, S, TX, TYT, RY, P>;
-  if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
+  static int per_sm = 0;
+  if (per_sm == 0) {
+    if (smem > 48 * 1024) {
+      cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+    }
+    per_sm = resident_per_sm(kern, TX * TYT, smem);
   }
+  int nzc = z_chunks(tiles, planes, per_sm, 4);
+  const int zc = (planes + nzc - 1) / nzc;
+  nzc = (planes + zc - 1) / zc;
   dim3 grid((nx + TX - 1) / TX, (ny + TY - 1) / TY, nzc);
   kern<<<grid, dim3(TX, TYT), smem, stream>>>(A, *tm, zc, spin_limit, extra_tx);
   return cudaGetLastError();

@@ -249,6 +249,23 @@ def test_exact_sum_scale_follows_the_state(variant, dims, shape, bc, factor):
     compare(g.numpy(), O.rk4(x, h, a, s, dt, 21, V, BCS[bc], order), "c128")
 
 
+@pytest.mark.parametrize("dims,shape", [(1, (37,)), (2, (19, 45)), (3, (9, 21, 70))])
+@pytest.mark.parametrize("variant", [2, 3])
+def test_stiff_potential_keeps_the_exact_sum_stages(dims, shape, variant):
+    """The exact-sum stencil's range depends on the state alone, not on the
+    potential: with V 1e5 times the usual one the context keeps the exact-sum
+    stages and meets the FP64 bar."""
+    psi, V = problem(shape, 93)
+    h, a, s, order = 0.3, 0.6, -1.0, 4
+    Vs = V * 1e5
+    dt = 0.2 * O.stability_bound(dims, h, a, order, float(np.max(Vs)), abs(s) * 1.7)
+    g = Integrator(psi, h, a, s, Vs, "msd", order, "c128")
+    g.set_kernel(variant)
+    assert g.kernel_in_use() in (2, 3)
+    g.step(21, dt)
+    compare(g.numpy(), O.rk4(psi, h, a, s, dt, 21, Vs, W.BC_MSD, order), "c128")
+
+
 @pytest.mark.parametrize("bc", ["dirichlet", "l0", "periodic"])
 @pytest.mark.parametrize("variant", [2, 3])
 @pytest.mark.parametrize("dims,shape", [(2, (19, 45)), (3, (9, 21, 70))])
