@@ -66,24 +66,28 @@ CHUNK = 56   # steps per frame in the end-to-end measurement (the 87x87x203 run'
 LAUNCHES_PER_STEP = {"c128": 17, "c64": 16, "c64_acc64": 16}
 
 # DRAM bytes (read + write) per RK4 step of the stage kernels on trap_vortex_3d_256x256x512, from one
-# ncu capture (profiles/rk4_step_256x256x512_traffic_and_launches.md), with the hash of the kernel
-# sources it was taken at: the figure is reported only while csrc_hash() still matches.
+# ncu capture (profiles/rk4_step_256x256x512_traffic_and_launches.md), with the hash of the 3D stage
+# path's sources it was taken at: the figure is reported only while csrc_hash() still matches.
 TRAFFIC_PER_STEP = {  # dtype -> (bytes per step, csrc hash of the capture)
-    "c128": (10819.8e6, None),
-    "c64": (5461.3e6, None),
-    "c64_acc64": (6230.8e6, None),
+    "c128": (10807.8e6, "3a6cd1835f42e611"),
+    "c64": (5446.4e6, "3a6cd1835f42e611"),
+    "c64_acc64": (6220.2e6, "3a6cd1835f42e611"),
 }
+
+# The sources the 3D stage path (deep kernels, wall slabs, scale update, step loop) is built from.
+STAGE3D_SOURCES = ("api.cu", "reduce.cu", "nlse_device.cuh", "nlse_internal.h", "stage_3d_impl.cuh",
+                   "stage_3d_p32_o2.cu", "stage_3d_p32_o4.cu", "stage_3d_p64_o2.cu", "stage_3d_p64_o4.cu",
+                   "stage_3d_pmix_o2.cu", "stage_3d_pmix_o4.cu", "stage_generic.cuh", "stage_slab.cuh",
+                   "stage_tiled.cuh", "stage_tma.cuh")
 
 
 def csrc_hash():
-    """sha256 (first 16 hex digits) over the CUDA sources and headers the kernels are built from."""
-    import glob
+    """sha256 (first 16 hex digits) over the sources of the 3D stage path."""
     import hashlib
     h = hashlib.sha256()
-    for f in sorted(glob.glob(os.path.join(ROOT, "paper_1203_1263_gb300", "csrc", "*")) +
-                    glob.glob(os.path.join(ROOT, "include", "*.h"))):
-        h.update(os.path.basename(f).encode())
-        h.update(open(f, "rb").read())
+    for name in STAGE3D_SOURCES:
+        h.update(name.encode())
+        h.update(open(os.path.join(ROOT, "paper_1203_1263_gb300", "csrc", name), "rb").read())
     return h.hexdigest()[:16]
 
 
@@ -603,7 +607,11 @@ def batch_form(args, dev, K, Wm):
 
     with torch.cuda.stream(stream):
         b = BatchIntegrator(runs, device=dev, stream=stream)
-        tile, _ = b.autotune()
+        if args.batch_tile is None:
+            tile, _ = b.autotune()
+        else:
+            tile = args.batch_tile
+            b.set_tile(tile)
         b.step(Wm)
         b.sync()
         t_batch = timed(b.step, K)
@@ -844,6 +852,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--batch-runs", type=int, default=512)
+    ap.add_argument("--batch-tile", type=int, default=None,
+                    help="batch deep-kernel tile shape (nlse_batch_set_tile 0..3; default: the autotuner's pick)")
     ap.add_argument("--no-surrogate", action="store_true")
     ap.add_argument("--sur-traj", type=int, default=160, help="surrogate training trajectories (125 windows each)")
     ap.add_argument("--sur-epochs", type=int, default=60)

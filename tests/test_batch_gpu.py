@@ -96,11 +96,12 @@ def test_switching_tiles_on_one_batch_keeps_results():
     changes; the status word must not, and every shape must continue the
     same integration."""
     runs = small_runs(seed=6, nruns=9)
+    tiles = (1, 3, 0, 2)
     ref = BatchIntegrator(runs)
-    ref.step(8)
+    ref.step(2 * len(tiles))
     ref.sync()
     b = BatchIntegrator(runs)
-    for t in (1, 3, 0, 2):
+    for t in tiles:
         b.set_tile(t)
         b.step(2)
         b.sync()
