@@ -145,11 +145,12 @@ __global__ void __launch_bounds__(1024) k_line1d(const __grid_constant__ LineArg
 
 namespace nlse {
 
-// The cluster for an n-site line: CL CTAs (16 at most, about 128 sites each at least) of seg sites, the
-// last one with at least 2 (the halo a neighbour copies); false when a segment does not fit in shared
-// memory (elem = bytes of one complex value).
+// The cluster for an n-site line: CL CTAs (16 at most, about 32 sites each at least, so that a stage's
+// per-site work is spread over as many SMs as the cluster allows) of seg sites, the last one with at
+// least 2 (the halo a neighbour copies); false when a segment does not fit in shared memory (elem =
+// bytes of one complex value).
 inline bool line_plan(int n, size_t elem, int* cl, int* seg, size_t* smem) {
-  int c = n / 128;
+  int c = n / 32;
   c = c < 1 ? 1 : (c > kLineMaxCluster ? kLineMaxCluster : c);
   for (; c >= 1; --c) {
     const int s = (n + c - 1) / c;
