@@ -81,6 +81,15 @@ STAGE3D_SOURCES = ("api.cu", "reduce.cu", "nlse_device.cuh", "nlse_internal.h", 
                    "stage_tiled.cuh", "stage_tma.cuh")
 
 
+def workload_dt(p):
+    """The bench workload's time step, the same in both arms: 0.8 x the RK4 stability bound with the
+    potential and the nonlinearity, 2 sqrt(2) / (a rho_L + max|V| + |s| max|Psi|^2), rho_L = 4d/h^2 (CD)
+    or 16d/(3h^2) (2SHOC)."""
+    rho = 4.0 * p.dims / p.h ** 2 if p.order == 2 else 16.0 * p.dims / (3.0 * p.h ** 2)
+    s_rho = abs(p.s) * float(np.max(np.abs(p.psi0))) ** 2
+    return 0.8 * 2.0 * math.sqrt(2.0) / (p.a * rho + p.vmax() + s_rho)
+
+
 def csrc_hash():
     """sha256 (first 16 hex digits) over the sources of the 3D stage path."""
     import hashlib
@@ -269,7 +278,7 @@ def run_ours(args, rank, world, local_rank):
 
     p = build_problem(args.workload)
     s_rho = abs(p.s) * float(np.max(np.abs(p.psi0))) ** 2
-    dt = 0.8 * max_dt(3, p.h, p.a, p.order, p.vmax(), s_rho)
+    dt = workload_dt(p)
     sites = p.sites
     stream = torch.cuda.Stream(dev)
 
@@ -692,7 +701,7 @@ def run_reference(args, rank, world):
     import oracle
     p = build_problem(args.workload)
     s_rho = abs(p.s) * float(np.max(np.abs(p.psi0))) ** 2
-    dt = 0.8 * oracle.stability_bound(3, p.h, p.a, p.order, p.vmax(), s_rho)
+    dt = workload_dt(p)
     cores = oracle.set_threads(os.cpu_count() or 1)
     # one bench step = one RK4 step on a z-slab sized to ~budget / (K + W) seconds
     per_step_budget = max(0.5, args.ref_budget / max(1, args.steps + args.warmup))
