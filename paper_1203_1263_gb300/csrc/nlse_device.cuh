@@ -605,22 +605,33 @@ __device__ __forceinline__ unsigned int serve_walls(const StageArgs<T>& A, const
     const R m2 = EXACT ? m2w : norm2(pc);
     if (EXACT ? m2 > R(0) : m2 > f.tiny) theta = fma(F.y, pc.x, -(F.x * pc.y)) / m2;
   }
-  // all offsets o in {-1, 0, 1}^D except 0, where -1 needs idx == 1 and +1 needs idx == n - 2
+  // all offsets o in {-1, 0, 1}^D except 0, where -1 needs idx == 1 and +1 needs idx == n - 2: per axis
+  // the options {0, -1 if idx == 1, +1 if idx == n - 2}, walked as a mixed-radix counter in a loop that
+  // is not unrolled, so the boundary-site update below is emitted once (a face site has one such
+  // neighbour, an edge three, a corner seven); each boundary site is updated on its own, so the order
+  // of the walk does not change any result
+  int opt[D][3], cnt[D], total = 1;
 #pragma unroll
-  for (int q = 1; q < (D == 1 ? 3 : (D == 2 ? 9 : 27)); ++q) {
+  for (int k = 0; k < D; ++k) {
+    cnt[k] = 1;
+    opt[k][0] = 0;
+    if (idx[k] == 1) opt[k][cnt[k]++] = -1;
+    if (idx[k] == f.n[k] - 2) opt[k][cnt[k]++] = 1;
+    total *= cnt[k];
+  }
+#pragma unroll 1
+  for (int q = 1; q < total; ++q) {
     int o[D];
     int r = q;
-    bool ok = true;
     int64_t b = c;
 #pragma unroll
     for (int k = D - 1; k >= 0; --k) {
-      const int v = r % 3;
-      r /= 3;
-      o[k] = (v == 2) ? -1 : v;
-      ok &= (o[k] == 0) | ((o[k] == -1) & (idx[k] == 1)) | ((o[k] == 1) & (idx[k] == f.n[k] - 2));
+      const int ck = cnt[k];
+      const int v = r % ck;
+      r /= ck;
+      o[k] = v == 0 ? 0 : (v == 1 ? opt[k][1] : opt[k][2]);
       b += o[k] * f.st[k];
     }
-    if (!ok) continue;
     C2 Fb = {R(0), R(0)};
     if (f.bc == BC_MSD) {
       const C2 pb = acc.atv(o);
