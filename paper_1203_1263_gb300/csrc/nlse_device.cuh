@@ -580,9 +580,9 @@ __device__ __forceinline__ unsigned int rk_apply(const StageArgs<T>& A, int64_t 
   return 0u;
 }
 
-template <class T>
+template <class T, int S = -1>
 __device__ __forceinline__ unsigned int rk_update(const StageArgs<T>& A, int64_t i, typename V2<typename T::R>::t F) {
-  return rk_apply<T>(A, i, F, load_point<T>(A, i, false));
+  return rk_apply<T, S>(A, i, F, load_point<T, S>(A, i, false));
 }
 
 // Update every boundary site whose b-1 neighbour is the interior site c
@@ -590,7 +590,8 @@ __device__ __forceinline__ unsigned int rk_update(const StageArgs<T>& A, int64_t
 // all 0), with F_b = 0 (Dirichlet), F_b = i Im(F_c / Psi_c) Psi_b (MSD) or
 // F_b = i N_b Psi_b (L0; in units of cLF on the exact-sum stages, like F_c).
 // Out of line: only sites next to a wall call it.
-template <class T, int D, bool EXACT, class Acc>
+// S: the RK4 stage when the caller's kernel is built for one (-1: A.stage at run time).
+template <class T, int D, bool EXACT, class Acc, int S = -1>
 __device__ __forceinline__ unsigned int serve_walls(const StageArgs<T>& A, const Acc& acc, const int* idx, int64_t c,
                                                  typename V2<typename T::R>::t pc, typename V2<typename T::R>::t F,
                                                  typename T::R m2w) {
@@ -641,7 +642,7 @@ __device__ __forceinline__ unsigned int serve_walls(const StageArgs<T>& A, const
       const R Nb = fma(EXACT ? f.sG : f.s, norm2(pb), -ldv<R>(EXACT ? A.Vs : f.V, b));
       Fb = {-Nb * pb.y, Nb * pb.x};
     }
-    ex = max(ex, rk_update<T>(A, b, Fb));
+    ex = max(ex, rk_update<T, S>(A, b, Fb));
   }
   return ex;
 }
@@ -649,7 +650,7 @@ __device__ __forceinline__ unsigned int serve_walls(const StageArgs<T>& A, const
 // The full per-site work: F at interior site c, its update, and the update of
 // every boundary site whose b-1 neighbour is c.  `p` holds c's pointwise
 // operands (load_point).
-template <class T, int D, int ORDER, bool EXACT, class Acc>
+template <class T, int D, int ORDER, bool EXACT, class Acc, int S = -1>
 __device__ __forceinline__ unsigned int process_site_pv(const StageArgs<T>& A, const Acc& acc, const int* idx,
                                                         int64_t c, const PointVals<T>& p) {
   using R = typename T::R;
@@ -669,19 +670,19 @@ __device__ __forceinline__ unsigned int process_site_pv(const StageArgs<T>& A, c
   if constexpr (EXACT) aL = a_lap_exact<T, D, ORDER>(f, acc, idx, c, pc, Nc, m2w);
   else aL = a_lap<T, D, ORDER>(f, acc, idx, c, pc, Nc);
   const C2 F = {-fma(Nc, pc.y, aL.y), fma(Nc, pc.x, aL.x)};
-  unsigned int ex = rk_apply<T>(A, c, F, p);
+  unsigned int ex = rk_apply<T, S>(A, c, F, p);
 
   bool near = false;
 #pragma unroll
   for (int k = 0; k < D; ++k) near |= (idx[k] == 1) | (idx[k] == f.n[k] - 2);
-  if (near) ex = max(ex, serve_walls<T, D, EXACT>(A, acc, idx, c, pc, F, m2w));
+  if (near) ex = max(ex, serve_walls<T, D, EXACT, Acc, S>(A, acc, idx, c, pc, F, m2w));
   return ex;
 }
 
-template <class T, int D, int ORDER, bool EXACT, class Acc>
+template <class T, int D, int ORDER, bool EXACT, class Acc, int S = -1>
 __device__ __forceinline__ unsigned int process_site(const StageArgs<T>& A, const Acc& acc, const int* idx,
                                                      int64_t c) {
-  return process_site_pv<T, D, ORDER, EXACT>(A, acc, idx, c, load_point<T, -1, EXACT>(A, c, true));
+  return process_site_pv<T, D, ORDER, EXACT, Acc, S>(A, acc, idx, c, load_point<T, S, EXACT>(A, c, true));
 }
 
 // ---------------------------------------------------------------------------

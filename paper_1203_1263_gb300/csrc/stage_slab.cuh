@@ -73,11 +73,12 @@ template <int NS> struct SlabShape {
 // NS sites per (marching, fast) position along the normal axis: low wall 1 .. NS,
 // high wall N-1-NS .. N-2.  Thread (tn, tf, tm), tn fastest, processes site
 // (m0 + tm, normal site tn, f0 + tf).
-template <class T, int ORDER, bool EXACT, int AXM, int AXN, int AXF, int NS>
+// S: the RK4 stage (compile time, so that only that stage's update is in the kernel's code).
+template <class T, int ORDER, bool EXACT, int AXM, int AXN, int AXF, int NS, int S>
 __global__ void __launch_bounds__(SlabShape<NS>::THREADS) k_stage_slab(const StageArgs<T> A, const SlabRange rg) {
   using C = typename T::C;
-  using S = SlabShape<NS>;
-  constexpr int WF = kSlabTF + 4, NWL = S::NWL, PL = NWL * WF, NP = S::MC + 4;
+  using Sh = SlabShape<NS>;
+  constexpr int WF = kSlabTF + 4, NWL = Sh::NWL, PL = NWL * WF, NP = Sh::MC + 4;
   __shared__ C win[NP * PL];
   const Field<T>& f = A.f;
   const int tid = threadIdx.x;
@@ -85,9 +86,9 @@ __global__ void __launch_bounds__(SlabShape<NS>::THREADS) k_stage_slab(const Sta
   const int n_win0 = hi ? f.n[AXN] - NWL : 0;        // first of the window's normal layers
   const int n_first = hi ? f.n[AXN] - 1 - NS : 1;    // first site layer
   const int f0 = rg.f_lo + blockIdx.x * kSlabTF;     // first site of this CTA along the fast axis
-  const int m0 = rg.m_lo + blockIdx.y * S::MC;       // first site along the marching axis
+  const int m0 = rg.m_lo + blockIdx.y * Sh::MC;       // first site along the marching axis
 
-  for (int e = tid; e < NP * PL; e += S::THREADS) {
+  for (int e = tid; e < NP * PL; e += Sh::THREADS) {
     const int pl = e / PL, r = e % PL;
     int nw, fw;
     if (AXF == 2) { nw = r / WF; fw = r % WF; }       // fast axis contiguous in memory
@@ -118,7 +119,7 @@ __global__ void __launch_bounds__(SlabShape<NS>::THREADS) k_stage_slab(const Sta
     acc.wf = WF;
     acc.o = (ns - n_win0) * WF + (tf + 2);
     acc.F = EXACT ? cur_fix(f) : 0;
-    ex = process_site<T, 3, ORDER, EXACT>(A, acc, idx, c);
+    ex = process_site<T, 3, ORDER, EXACT, SlabAcc<T, AXM, AXN, AXF>, S>(A, acc, idx, c);
   }
   if (A.emax) emax_commit(A.emax, ex);
 }
@@ -127,9 +128,15 @@ inline bool slab_ok(const int* n) { return n[0] >= 7 && n[1] >= 7 && n[2] >= 10;
 
 template <class T, int ORDER, bool EXACT, int AXM, int AXN, int AXF, int NS>
 cudaError_t launch_slab(const StageArgs<T>& A, const SlabRange& rg, cudaStream_t stream) {
-  using S = SlabShape<NS>;
-  const dim3 grid((unsigned)((rg.f_hi - rg.f_lo) / kSlabTF + 1), (unsigned)((rg.m_hi - rg.m_lo) / S::MC + 1), 2);
-  k_stage_slab<T, ORDER, EXACT, AXM, AXN, AXF, NS><<<grid, S::THREADS, 0, stream>>>(A, rg);
+  using Sh = SlabShape<NS>;
+  const dim3 grid((unsigned)((rg.f_hi - rg.f_lo) / kSlabTF + 1), (unsigned)((rg.m_hi - rg.m_lo) / Sh::MC + 1), 2);
+  switch (A.stage) {
+    case 1: k_stage_slab<T, ORDER, EXACT, AXM, AXN, AXF, NS, 1><<<grid, Sh::THREADS, 0, stream>>>(A, rg); break;
+    case 2: k_stage_slab<T, ORDER, EXACT, AXM, AXN, AXF, NS, 2><<<grid, Sh::THREADS, 0, stream>>>(A, rg); break;
+    case 3: k_stage_slab<T, ORDER, EXACT, AXM, AXN, AXF, NS, 3><<<grid, Sh::THREADS, 0, stream>>>(A, rg); break;
+    case 4: k_stage_slab<T, ORDER, EXACT, AXM, AXN, AXF, NS, 4><<<grid, Sh::THREADS, 0, stream>>>(A, rg); break;
+    default: k_stage_slab<T, ORDER, EXACT, AXM, AXN, AXF, NS, -1><<<grid, Sh::THREADS, 0, stream>>>(A, rg); break;
+  }
   return cudaGetLastError();
 }
 
