@@ -119,6 +119,8 @@ struct nlse_ctx {
   bool line_failed;               // the 1D cluster path could not be launched here: per-site kernel instead
   cudaStream_t side;              // wall-shell kernels run here, concurrently with the deep kernels
   cudaEvent_t ev_fork, ev_join;
+  cudaStream_t side_yx[2];        // 3D: the y- and x-wall slabs' streams
+  cudaEvent_t ev_join_yx[2];
 
   void* at(size_t off) const { return ws + off; }
   unsigned int* flag() const { return (unsigned int*)(ws + lay.status); }
@@ -307,6 +309,10 @@ LaunchCfg launch_cfg(const nlse_ctx* c) {
   L.side = c->side;
   L.ev_fork = c->ev_fork;
   L.ev_join = c->ev_join;
+  for (int i = 0; i < 2; ++i) {
+    L.side_yx[i] = c->side_yx[i];
+    L.ev_join_yx[i] = c->ev_join_yx[i];
+  }
   return L;
 }
 
@@ -532,6 +538,10 @@ int nlse_create(nlse_t* out, int dims, const int64_t* N, double h, double a, dou
     e = cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming);
+    for (int i = 0; i < 2 && e == cudaSuccess && dims == 3; ++i) {
+      e = cudaStreamCreateWithFlags(&c->side_yx[i], cudaStreamNonBlocking);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_join_yx[i], cudaEventDisableTiming);
+    }
   }
   // Exact-sum stencil reference scale F0: the largest component of Psi0 below
   // 2^53 in fixed point (operands are accepted below 2^55).
@@ -832,6 +842,10 @@ int nlse_destroy(nlse_t c) {
   if (!c) return NLSE_OK;
   drop_graph(c);
   if (c->cap) cudaStreamDestroy(c->cap);
+  for (int i = 0; i < 2; ++i) {
+    if (c->side_yx[i]) cudaStreamDestroy(c->side_yx[i]);
+    if (c->ev_join_yx[i]) cudaEventDestroy(c->ev_join_yx[i]);
+  }
   if (c->side) cudaStreamDestroy(c->side);
   if (c->ev_fork) cudaEventDestroy(c->ev_fork);
   if (c->ev_join) cudaEventDestroy(c->ev_join);

@@ -18,7 +18,7 @@ cudaError_t launch_fused_step(const StageArgs<P32>* A, const void* tm12, const v
       return pass == 0 ? launch_fused_kernel<ORDER, 1>(A1, A2, tm, L.spin_limit, L.extra_tx, st)
                        : launch_fused_kernel<ORDER, 3>(A1, A2, tm, L.spin_limit, L.extra_tx, st);
     };
-    auto shell = [&](cudaStream_t st) -> cudaError_t { return launch_shell_slabs<P32, ORDER, false, 3>(B1, st); };
+    auto shell = [&](cudaStream_t st) -> cudaError_t { return launch_shell_slabs<P32, ORDER, false, 3>(B1, st, L.side_yx); };
     cudaError_t e = launch_deep_and_shell(L, stream, true, deep, shell);
     if (e != cudaSuccess) return e;
     if ((e = launch_shell_slabs3<ORDER>(A2, stream)) != cudaSuccess) return e;

@@ -44,13 +44,16 @@ cudaError_t launch_stage(const StageArgs<T>& A, const LaunchCfg& L, cudaStream_t
       return launch_shell_periodic<T, D, ORDER>(B, st);
     }
     if (slabs) {
-      if constexpr (fp64) if (exact) return launch_shell_slabs<T, ORDER, true, nsx>(B, st);
-      return launch_shell_slabs<T, ORDER, false, nsx>(B, st);
+      if constexpr (fp64) if (exact) return launch_shell_slabs<T, ORDER, true, nsx>(B, st, L.side_yx);
+      return launch_shell_slabs<T, ORDER, false, nsx>(B, st, L.side_yx);
     }
     if constexpr (fp64) if (exact) return launch_shell<T, D, ORDER, true>(B, st);
     return launch_shell<T, D, ORDER>(B, st);
   };
-  return launch_deep_and_shell(L, stream, has_deep(D, A.f.m), deep, shell);
+  if (slabs) return launch_deep_and_shell(L, stream, has_deep(D, A.f.m), deep, shell);
+  LaunchCfg L1 = L;   // one shell kernel: no use for the slabs' extra streams
+  L1.side_yx[0] = L1.side_yx[1] = nullptr;
+  return launch_deep_and_shell(L1, stream, has_deep(D, A.f.m), deep, shell);
 }
 
 }  // namespace nlse

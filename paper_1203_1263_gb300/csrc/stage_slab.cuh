@@ -143,18 +143,21 @@ cudaError_t launch_slab(const StageArgs<T>& A, const SlabRange& rg, cudaStream_t
 // The whole 3D shell as three slab launches (axes: 0 = z, 1 = y, 2 = x); with
 // NSX = 3 x-wall layers the caller's deep-interior kernels must run with
 // xwall = 2, with NSX = 1 with xwall = 0.
+// yx: if given, the y- and x-wall slabs go to yx[0] and yx[1] (all three slabs then run concurrently).
 template <class T, int ORDER, bool EXACT, int NSX>
-cudaError_t launch_shell_slabs(const StageArgs<T>& A, cudaStream_t stream) {
+cudaError_t launch_shell_slabs(const StageArgs<T>& A, cudaStream_t stream, const cudaStream_t* yx = nullptr) {
   const int* n = A.f.n;
   cudaError_t e;
   // z walls: march y over [1, Ny-2], fast x over [1, Nx-2]
   if ((e = launch_slab<T, ORDER, EXACT, 1, 0, 2, 1>(A, SlabRange{1, n[1] - 2, 1, n[2] - 2}, stream)) != cudaSuccess)
     return e;
   // y walls: march z over [2, Nz-3], fast x over [1, Nx-2]
-  if ((e = launch_slab<T, ORDER, EXACT, 0, 1, 2, 1>(A, SlabRange{2, n[0] - 3, 1, n[2] - 2}, stream)) != cudaSuccess)
+  if ((e = launch_slab<T, ORDER, EXACT, 0, 1, 2, 1>(A, SlabRange{2, n[0] - 3, 1, n[2] - 2},
+                                                    yx && yx[0] ? yx[0] : stream)) != cudaSuccess)
     return e;
   // x walls (NSX layers each): march z over [2, Nz-3], fast y over [2, Ny-3]
-  return launch_slab<T, ORDER, EXACT, 0, 2, 1, NSX>(A, SlabRange{2, n[0] - 3, 2, n[1] - 3}, stream);
+  return launch_slab<T, ORDER, EXACT, 0, 2, 1, NSX>(A, SlabRange{2, n[0] - 3, 2, n[1] - 3},
+                                                    yx && yx[1] ? yx[1] : stream);
 }
 
 }  // namespace nlse
