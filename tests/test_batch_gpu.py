@@ -107,3 +107,51 @@ def test_switching_tiles_on_one_batch_keeps_results():
         b.sync()
     for i in range(len(runs)):
         assert np.array_equal(b.numpy(i), ref.numpy(i)), i
+
+
+def workload_runs(nruns=512, seed=4):
+    """The timed batch workload itself: 512 runs of sides 64..1024 (2.0e8
+    sites), each at 0.8 of its own stability bound, Dirichlet walls."""
+    runs = []
+    for d in W.batch_runs_2d(nruns=nruns, seed=seed):
+        p = W.batch_run_problem(d)
+        s_rho = abs(p.s) * float(np.max(np.abs(p.psi0))) ** 2
+        dt = 0.8 * O.stability_bound(2, p.h, p.a, p.order, p.vmax(), s_rho)
+        runs.append(dict(psi0=p.psi0, h=p.h, a=p.a, s=p.s, dt=dt, V=p.V, bc="dirichlet", order=p.order))
+    return runs
+
+
+def test_full_batch_workload_matches_oracle():
+    """Every run of the full 512-run workload (the benchmark's sides, launch
+    configuration and tile autotuner) over 5 steps against the FP64 oracle."""
+    runs = workload_runs()
+    b = BatchIntegrator(runs)
+    b.autotune()
+    b.step(5)
+    b.sync()
+    worst = 0.0
+    for i, r in enumerate(runs):
+        ref = O.rk4(r["psi0"], r["h"], r["a"], r["s"], r["dt"], 5, r["V"], BCS[r["bc"]], r["order"])
+        got = b.numpy(i).astype(np.complex128)
+        err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+        worst = max(worst, err)
+        assert err <= 2e-5, (i, r["psi0"].shape, err)
+    print(f"512 runs, 5 steps: largest relative L2 {worst:.2e}")
+
+
+def test_batch_workload_runs_full_length_match_oracle():
+    """The four smallest runs of the workload's recipe and its largest one,
+    batched together over the workload's full 1000 steps, against the FP64
+    oracle."""
+    runs = workload_runs()
+    sides = np.array([r["psi0"].shape[0] for r in runs])
+    pick = list(np.argsort(sides, kind="stable")[:4]) + [int(np.argmax(sides))]
+    sub = [runs[i] for i in pick]
+    b = BatchIntegrator(sub)
+    b.step(1000)
+    b.sync()
+    for i, r in enumerate(sub):
+        ref = O.rk4(r["psi0"], r["h"], r["a"], r["s"], r["dt"], 1000, r["V"], BCS[r["bc"]], r["order"])
+        got = b.numpy(i).astype(np.complex128)
+        err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+        assert err <= 2e-5, (pick[i], r["psi0"].shape, err)
