@@ -69,9 +69,9 @@ LAUNCHES_PER_STEP = {"c128": 17, "c64": 16, "c64_acc64": 16}
 # ncu capture (profiles/rk4_step_256x256x512_traffic_and_launches.md), with the hash of the 3D stage
 # path's sources it was taken at: the figure is reported only while csrc_hash() still matches.
 TRAFFIC_PER_STEP = {  # dtype -> (bytes per step, csrc hash of the capture)
-    "c128": (10807.8e6, "3a6cd1835f42e611"),
-    "c64": (5446.4e6, "3a6cd1835f42e611"),
-    "c64_acc64": (6220.2e6, "3a6cd1835f42e611"),
+    "c128": (10875.0e6, "1b4f1a7eff1cc6be"),
+    "c64": (5536.7e6, "1b4f1a7eff1cc6be"),
+    "c64_acc64": (6315.0e6, "1b4f1a7eff1cc6be"),
 }
 
 # The sources the 3D stage path (deep kernels, wall slabs, scale update, step loop) is built from.
@@ -384,7 +384,8 @@ def run_ours(args, rank, world, local_rank):
             forms["rings512"] = {k: details["rings_512cube"][k] for k in ("c128", "c64_acc64", "x_f64",
                                                                          "rel_l2_after_steps")}
         details["soliton_1d_2001"] = soliton_form(dev)
-        forms["soliton1d"] = {k: details["soliton_1d_2001"][k]["us_per_step"] for k in ("c128", "c64")}
+        forms["soliton1d"] = {f"us_per_step_{k}": details["soliton_1d_2001"][k]["us_per_step"]
+                              for k in ("c128", "c64")}
 
     if not args.no_batch and rank == 0:
         details["batch"] = batch_form(args, dev, min(K, 200), Wm)
