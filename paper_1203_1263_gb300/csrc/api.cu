@@ -522,6 +522,11 @@ int nlse_create(nlse_t* out, int dims, const int64_t* N, double h, double a, dou
   c->variant = (dtype == NLSE_C128) ? 2 : 1;
   if (dims == 3 && total <= (dtype == NLSE_C128 ? (int64_t(1) << 18) : (int64_t(1) << 21)))
     c->variant = (dtype == NLSE_C128) ? 3 : 0;
+  // FP64 1D lines that fit one thread-block cluster: the FP64 stencil.  There each SM sub-partition runs
+  // one warp of the line, so a stage is bound by the latency of that warp's instruction chain, which the
+  // exact-sum stencil's conversions lengthen, not by the FP64 pipe's throughput (2001 sites, 2SHOC:
+  // 14.3 against 19.7 us per step; CD: 8.2 against 11.8).
+  if (dims == 1 && dtype == NLSE_C128 && line_ok(int(N[0]), true)) c->variant = 1;
   c->tile_cfg = -1;
   c->spin_limit = kSpinLimit;
   c->graph_dt = -1.0;
@@ -585,7 +590,7 @@ int nlse_set_kernel(nlse_t c, int variant, int tile_cfg) {
 int nlse_kernel_in_use(nlse_t c) {
   if (!c) return fail(NLSE_EINVAL, "NULL context");
   if (fused_path(c)) return 4;
-  if (line_path(c)) return c->dtype == NLSE_C128 ? 2 : 1;
+  if (line_path(c)) return c->exact() ? 2 : 1;
   if (c->variant == 4) return c->d == 1 ? 0 : 1;
   if (c->d == 1) return (c->dtype == NLSE_C128 && c->variant >= 2) ? 3 : 0;
   if (c->dtype != NLSE_C128 && c->variant >= 2) return c->variant - 2;

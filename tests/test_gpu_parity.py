@@ -180,22 +180,26 @@ def test_tiled_kernel_equals_generic_bitwise(dtype, dims, shape, tile_cfg):
 @pytest.mark.parametrize("n", [37, 1000, 2001, 5003, 60000])
 @pytest.mark.parametrize("bc", ["dirichlet", "msd", "l0", "periodic"])
 @pytest.mark.parametrize("order", [2, 4])
-@pytest.mark.parametrize("dtype", ["c128", "c64"])
-def test_line_cluster_equals_per_site_bitwise(n, bc, order, dtype):
+@pytest.mark.parametrize("dtype,family", [("c128", "exact"), ("c128", "fp64"), ("c64", "fp32")])
+def test_line_cluster_equals_per_site_bitwise(n, bc, order, dtype, family):
     """1D: the thread-block-cluster path (the whole call in one launch, the
-    line in shared memory) gives the per-site kernel's bits, also when the
-    steps are split across calls; lines too long for shared memory (60,000
-    sites in FP64) take the per-site kernel."""
+    line in shared memory) gives the per-site kernel's bits, with either FP64
+    stencil and also when the steps are split across calls; lines too long for
+    shared memory (60,000 sites in FP64) take the per-site kernel."""
     psi, V = problem((n,), 65, bc=bc)
     h, a, s = 0.3, 0.6, -1.0
     dt = stable_dt((n,), h, a, s, order, V)
-    per_site, line = (3, 2) if dtype == "c128" else (0, 1)
+    per_site, line = (3, 2) if family == "exact" else (0, 1)
     res = []
     for variant, split in ((per_site, (21,)), (line, (21,)), (line, (5, 16))):
         g = Integrator(psi, h, a, s, V, bc, order, dtype)
         g.set_kernel(variant)
         fits = not (dtype == "c128" and n > 49152)
         assert g.kernel_in_use() == (line if variant == line and fits else per_site)
+        if variant == line:
+            d = Integrator(psi, h, a, s, V, bc, order, dtype)   # the default: the FP64 stencil where it fits
+            assert d.kernel_in_use() == (1 if fits else (3 if dtype == "c128" else 0))
+            d.close()
         for k in split:
             g.step(k, dt)
         g.sync()
