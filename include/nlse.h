@@ -171,11 +171,12 @@ const char *nlse_last_error(void);
  *       in 64-bit fixed point on the integer pipe and converted to FP64 once,
  *   3 = generic kernel with the exact-sum stencil (NLSE_C128; else as 0).
  * Variants 0 and 1 give bit-for-bit the same result, and so do 2 and 3.
- * Default: 2 for NLSE_C128 and 1 otherwise, except 3D grids of at most 2^18
- * sites (NLSE_C128) or 2^21 sites (the FP32 forms), which take 3 and 0, and
- * NLSE_C128 1D lines short enough for the cluster path, which take 1 (the
- * cluster runs one warp per SM sub-partition there, so the stage is bound by
- * that warp's chain of dependent instructions, not by the FP64 pipe).
+ * Default: 2 for NLSE_C128 and 1 otherwise, except on grids small enough
+ * that a step is bound by latency rather than by throughput: 3D grids of at
+ * most 2^15 sites (NLSE_C128) or 2^17 sites (the FP32 forms) take 0, and
+ * NLSE_C128 2D grids of at most 80,000 sites and NLSE_C128 1D lines short
+ * enough for the cluster path take 1 (the plain FP64 stencil's instruction
+ * chain is shorter than the exact-sum stencil's conversions).
  * The exact-sum stencil's fixed-point scale follows the state: before every
  * step it is taken from the largest component of Psi (every component
  * below 2^53 in fixed point, 4x below the accepted range, so the largest

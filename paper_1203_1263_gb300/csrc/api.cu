@@ -516,16 +516,18 @@ int nlse_create(nlse_t* out, int dims, const int64_t* N, double h, double a, dou
   c->stream = (cudaStream_t)stream;
   c->ws = (char*)workspace;
   c->lay = L;
-  // FP64: exact-sum stencil.  3D grids too small to fill the GPU with the
-  // z-marching kernel's tiles x plane chunks take the one-thread-per-site
-  // kernel (measured faster up to about 2^18 sites in FP64, 2^21 in FP32).
+  // Default kernel per form and size, from timings of the paper's workloads (MSD, 2SHOC, us per step):
+  // FP64 takes the exact-sum stencil on the tiled kernels, except where the grid is so small that a
+  // step is bound by latency, not by the FP64 pipe's throughput, and the plain FP64 stencil's shorter
+  // instruction chain wins: 3D grids of at most 2^15 sites (one thread per site; 21^3: 62.6 against
+  // 93.7 for the tiled exact-sum kernel, 32^3: 67.2 against 95.9; 36^3: 89.7 against 86.3), 2D grids of
+  // at most 80,000 sites (tiled; 100^2: 32.9 against 51.7, 282^2: 49.7 against 56.6; 316^2: 61.1
+  // against 54.0) and 1D lines short enough for the cluster path (2001 sites: 14.3 against 19.7).  The
+  // FP32 forms take the tiled kernel on 3D grids above 2^17 sites (64^3: 41.8 against 47.1 for one
+  // thread per site, 128^3: 88.3 against 176.8; 46^3: 39.2 against 34.5).
   c->variant = (dtype == NLSE_C128) ? 2 : 1;
-  if (dims == 3 && total <= (dtype == NLSE_C128 ? (int64_t(1) << 18) : (int64_t(1) << 21)))
-    c->variant = (dtype == NLSE_C128) ? 3 : 0;
-  // FP64 1D lines that fit one thread-block cluster: the FP64 stencil.  There each SM sub-partition runs
-  // one warp of the line, so a stage is bound by the latency of that warp's instruction chain, which the
-  // exact-sum stencil's conversions lengthen, not by the FP64 pipe's throughput (2001 sites, 2SHOC:
-  // 14.3 against 19.7 us per step; CD: 8.2 against 11.8).
+  if (dims == 3 && total <= (dtype == NLSE_C128 ? (int64_t(1) << 15) : (int64_t(1) << 17))) c->variant = 0;
+  if (dims == 2 && dtype == NLSE_C128 && total <= 80000) c->variant = 1;
   if (dims == 1 && dtype == NLSE_C128 && line_ok(int(N[0]), true)) c->variant = 1;
   c->tile_cfg = -1;
   c->spin_limit = kSpinLimit;

@@ -287,16 +287,19 @@ def test_exact_sum_out_of_range_falls_back(variant, dims, shape, bc):
     compare(g.numpy(), O.rk4(psi, h, a, s, dt, 4, V, BCS[bc], order), "c128")
 
 
-@pytest.mark.parametrize("dtype", ["c128", "c64", "c64_acc64"])
-def test_refresh_potential_takes_new_values(dtype):
+@pytest.mark.parametrize("dtype,variant", [("c128", None), ("c128", 2), ("c64", None), ("c64_acc64", None)])
+def test_refresh_potential_takes_new_values(dtype, variant):
     """V written after creation takes effect after nlse_refresh_potential, in
-    every dtype alike (the FP64 stages' scaled copy and max|V| are re-read)."""
+    every dtype alike (max|V| and, on the exact-sum stages, the scaled copy
+    V / cLF are re-read)."""
     shape = (9, 21, 70)
     psi, V = problem(shape, 41)
     V2 = 2.0 * V + 0.1
     h, a, s, order = 0.3, 0.6, -1.0, 4
     dt = stable_dt(shape, h, a, s, order, V2)
     g = Integrator(psi, h, a, s, V, "msd", order, dtype)
+    if variant is not None:
+        g.set_kernel(variant)
     g.V.copy_(torch.from_numpy(V2).to(g.V.dtype).to(g.V.device))
     between = 0.5 * (O.stability_bound(3, h, a, order, float(np.max(V)), 0.0) +
                      O.stability_bound(3, h, a, order, float(np.max(V2)), 0.0))
@@ -366,17 +369,19 @@ def test_autotune_picks_a_tile_and_keeps_results(dtype, tmp_path, monkeypatch):
 
 @pytest.mark.parametrize("dtype", ["c128", "c64"])
 def test_small_3d_grid_defaults_to_the_per_site_kernel(dtype):
-    """A 3D grid too small for the z-marching kernel's tiles defaults to the
-    one-thread-per-site kernel (nothing for the autotuner to time), with the
-    same result as the tiled kernel of its arithmetic."""
+    """A 3D grid small enough to be latency-bound (30,240 sites) defaults to
+    the one-thread-per-site kernel with the plain stencil (nothing for the
+    autotuner to time), with the same result as the tiled kernel of its
+    arithmetic."""
     psi, V = problem((14, 30, 72), 23)
     h, a, s, order = 0.3, 0.6, -1.0, 4
     dt = stable_dt(psi.shape, h, a, s, order, V)
     g = Integrator(psi, h, a, s, V, "msd", order, dtype)
     assert g.autotune() == (-1, 0.0)
     g.step(6, dt)
+    assert g.kernel_in_use() == 0
     t = Integrator(psi, h, a, s, V, "msd", order, dtype)
-    t.set_kernel(2 if dtype == "c128" else 1)
+    t.set_kernel(1)
     t.step(6, dt)
     assert np.array_equal(g.numpy(), t.numpy())
 
