@@ -69,9 +69,9 @@ LAUNCHES_PER_STEP = {"c128": 17, "c64": 16, "c64_acc64": 16}
 # ncu capture (profiles/rk4_step_256x256x512_traffic_and_launches.md), with the hash of the 3D stage
 # path's sources it was taken at: the figure is reported only while csrc_hash() still matches.
 TRAFFIC_PER_STEP = {  # dtype -> (bytes per step, csrc hash of the capture)
-    "c128": (10875.0e6, "1b4f1a7eff1cc6be"),
-    "c64": (5536.7e6, "1b4f1a7eff1cc6be"),
-    "c64_acc64": (6315.0e6, "1b4f1a7eff1cc6be"),
+    "c128": (10875.0e6, "ffb04f0babceec4d"),
+    "c64": (5536.7e6, "ffb04f0babceec4d"),
+    "c64_acc64": (6315.0e6, "ffb04f0babceec4d"),
 }
 
 # The sources the 3D stage path (deep kernels, wall slabs, scale update, step loop) is built from.
