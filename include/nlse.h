@@ -173,10 +173,11 @@ const char *nlse_last_error(void);
  * Variants 0 and 1 give bit-for-bit the same result, and so do 2 and 3.
  * Default: 2 for NLSE_C128 and 1 otherwise, except on grids small enough
  * that a step is bound by latency rather than by throughput: 3D grids of at
- * most 2^15 sites (NLSE_C128) or 2^17 sites (the FP32 forms) take 0, and
- * NLSE_C128 2D grids of at most 80,000 sites and NLSE_C128 1D lines short
- * enough for the cluster path take 1 (the plain FP64 stencil's instruction
- * chain is shorter than the exact-sum stencil's conversions).
+ * most 2^15 sites (NLSE_C128) or 2^17 sites (the FP32 forms) take 0,
+ * NLSE_C128 2D grids of at most 80,000 sites take 1, and NLSE_C128 1D lines
+ * take 1 (the cluster path) up to 2500 sites, 0 up to 2^15 sites and 3
+ * beyond (the plain FP64 stencil's instruction chain is shorter than the
+ * exact-sum stencil's conversions; a cluster's 16 SMs bound longer lines).
  * The exact-sum stencil's fixed-point scale follows the state: before every
  * step it is taken from the largest component of Psi (every component
  * below 2^53 in fixed point, 4x below the accepted range, so the largest

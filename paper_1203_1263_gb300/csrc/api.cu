@@ -523,13 +523,17 @@ int nlse_create(nlse_t* out, int dims, const int64_t* N, double h, double a, dou
   // instruction chain wins: 3D grids of at most 2^15 sites (one thread per site; 21^3: 62.6 against
   // 93.7 for the tiled exact-sum kernel, 32^3: 67.2 against 95.9; 36^3: 89.7 against 86.3), 2D grids of
   // at most 80,000 sites (tiled; 100^2: 32.9 against 51.7, 282^2: 49.7 against 56.6; 316^2: 61.1
-  // against 54.0) and 1D lines short enough for the cluster path (2001 sites: 14.3 against 19.7).  The
-  // FP32 forms take the tiled kernel on 3D grids above 2^17 sites (64^3: 41.8 against 47.1 for one
+  // against 54.0) and 1D lines: up to 2500 sites on the cluster path (2001 sites: 14.3 against 19.7
+  // with the exact-sum stencil, 18.1 against 19.4 for one thread per site on the dark soliton), up to
+  // 2^15 sites one thread per site (beyond ~2500 sites the cluster's 16 SMs bound it: 10,000 sites 34.8
+  // against 19.0; 20,000: 21.5 against 23.8 with the exact-sum stencil; 100,000: 36.9 against 29.0).
+  // The FP32 forms take the tiled kernel on 3D grids above 2^17 sites (64^3: 41.8 against 47.1 for one
   // thread per site, 128^3: 88.3 against 176.8; 46^3: 39.2 against 34.5).
   c->variant = (dtype == NLSE_C128) ? 2 : 1;
   if (dims == 3 && total <= (dtype == NLSE_C128 ? (int64_t(1) << 15) : (int64_t(1) << 17))) c->variant = 0;
   if (dims == 2 && dtype == NLSE_C128 && total <= 80000) c->variant = 1;
-  if (dims == 1 && dtype == NLSE_C128 && line_ok(int(N[0]), true)) c->variant = 1;
+  if (dims == 1 && dtype == NLSE_C128)
+    c->variant = (total <= 2500 && line_ok(int(N[0]), true)) ? 1 : (total <= (int64_t(1) << 15) ? 0 : 3);
   c->tile_cfg = -1;
   c->spin_limit = kSpinLimit;
   c->graph_dt = -1.0;

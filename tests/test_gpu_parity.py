@@ -197,8 +197,11 @@ def test_line_cluster_equals_per_site_bitwise(n, bc, order, dtype, family):
         fits = not (dtype == "c128" and n > 49152)
         assert g.kernel_in_use() == (line if variant == line and fits else per_site)
         if variant == line:
-            d = Integrator(psi, h, a, s, V, bc, order, dtype)   # the default: the FP64 stencil where it fits
-            assert d.kernel_in_use() == (1 if fits else (3 if dtype == "c128" else 0))
+            d = Integrator(psi, h, a, s, V, bc, order, dtype)   # the default kernel for this length
+            if dtype == "c128":   # the cluster up to 2500 sites, then one thread per site, FP64 stencil to 2^15
+                assert d.kernel_in_use() == (1 if n <= 2500 else (0 if n <= 32768 else 3))
+            else:
+                assert d.kernel_in_use() == 1
             d.close()
         for k in split:
             g.step(k, dt)
